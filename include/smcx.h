@@ -1,0 +1,212 @@
+/*
+ * smcx.h -- C ABI of the GB300 SMC-X swap-sweep library (libsmcx.so).
+ *
+ * The library runs the hot path of SMC-X (arXiv 2509.20949) with the EPI
+ * model: Metropolis swap trials (Sec. 2.1, Eq. 3) over a checkerboard of
+ * link cells whose origin moves every MC step (Sec. 2.2, Eq. 5), each trial's
+ * energy change taken from the local interaction zone of the swapped pair
+ * (Sec. 2.2) with pairwise shell interactions only (Sec. 3, EPI model), plus
+ * the Warren-Cowley short-range order (Sec. 3.2, Eq. 9) and the total energy.
+ *
+ * Conventions shared by every call:
+ *  - Every function returns an smcx_status; nothing throws or longjmps across
+ *    the ABI.  On failure smcx_last_error() (per host thread) describes why.
+ *    Errors of a call that ran on the GPU (SMCX_ECUDA, SMCX_ETIMEOUT) are
+ *    sticky on the handle: later calls return SMCX_ESTATE until destroy.
+ *  - Memory ownership: the caller owns every device buffer (occupancy,
+ *    workspace) and the CUDA stream; the library keeps non-owning pointers
+ *    and never calls cudaMalloc/cudaFree.  Host pointers are only read or
+ *    written during the call.
+ *  - Canonical occupancy layout (what crosses the ABI on the host side): one
+ *    byte per site holding the species id in [0, K), site index
+ *    ((z*n_y + y)*n_x + x)*nb + b, nb = 2 (BCC basis (0,0,0),(1,1,1)) or
+ *    4 (FCC basis (0,0,0),(0,1,1),(1,0,1),(1,1,0)), positions in half units
+ *    2*(x,y,z) + basis.  The lattice is periodic in all three directions.
+ *  - Energies are int64 in units of q = 2^-32 eV.  EPI tables are
+ *    [n_shells][K][K] int64, symmetric, shells in ascending distance
+ *    (BCC squared lengths 3,4,8,11; FCC 2,4,6,8 in (a/2)^2).
+ *  - Stream order: calls enqueue on the handle's stream; calls that return
+ *    host-visible results synchronise that stream before returning.
+ *  - One handle is used by one host thread at a time.
+ */
+#ifndef SMCX_H
+#define SMCX_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  SMCX_OK = 0,
+  SMCX_EINVAL = 1,    /* bad argument: sizes, species id >= K, asymmetric V, ... */
+  SMCX_ENOMEM = 2,    /* a caller buffer is too small */
+  SMCX_ECUDA = 3,     /* a CUDA runtime call or kernel failed */
+  SMCX_EOVERFLOW = 4, /* an energy total does not fit int64 */
+  SMCX_ETIMEOUT = 5,  /* a bounded device-side wait gave up */
+  SMCX_ESTATE = 6,    /* call not valid in the handle's state (no EPI yet, sticky error) */
+  SMCX_EBUDGET = 7    /* batch admission refused: memory budget or slots exhausted */
+} smcx_status;
+
+#define SMCX_BCC 0u
+#define SMCX_FCC 1u
+
+/* smcx_lattice_desc.flags */
+#define SMCX_NO_SHIFT 1u     /* keep the link-cell origin fixed (no per-step shift) */
+#define SMCX_SINGLE_CELL 2u  /* one link cell: fully sequential sweeps (tiny lattices) */
+
+typedef struct smcx_lattice smcx_lattice; /* opaque handle */
+
+typedef struct {
+  uint32_t kind;      /* SMCX_BCC or SMCX_FCC */
+  uint32_t n[3];      /* conventional cells per dimension (periodic), each >= 1 */
+  uint32_t n_species; /* K: 1..255 (1..16 when pack_bits == 4) */
+  uint32_t pack_bits; /* device storage: 8 (one byte per site) or 4 (two sites per byte) */
+  uint32_t min_cell;  /* link-cell edge floor in conventional cells; 0 = smallest safe edge */
+  uint32_t flags;     /* SMCX_NO_SHIFT | SMCX_SINGLE_CELL */
+  uint64_t seed;      /* Philox key (low word, high word) */
+} smcx_lattice_desc;
+
+typedef struct {
+  uint64_t attempts; /* trials made (one per site per sweep, Sec. 2.1) */
+  uint64_t unlike;   /* trials whose two sites held different species */
+  uint64_t accepted; /* accepted swaps */
+  int64_t sum_dE_q;  /* sum of the accepted energy changes (q units) */
+} smcx_sweep_stats;
+
+/* ---- sizes --------------------------------------------------------------- */
+
+/* Device bytes the caller must provide for the occupancy (rounded up to 16).
+   Returns 0 for an invalid descriptor. */
+size_t smcx_occupancy_bytes(const smcx_lattice_desc* desc);
+
+/* Device bytes the caller must provide as workspace (counters, EPI tables,
+   pair-count accumulators).  Returns 0 for an invalid descriptor. */
+size_t smcx_workspace_bytes(const smcx_lattice_desc* desc);
+
+/* ---- lattice life cycle ------------------------------------------------- */
+
+/* Validates desc and h_init (N = nb*n_x*n_y*n_z bytes, canonical layout,
+   every id < K), binds the caller's device buffers d_occ
+   (smcx_occupancy_bytes) and d_work (smcx_workspace_bytes, 256-byte
+   aligned) and the stream (a cudaStream_t, NULL = legacy default stream),
+   uploads the configuration and sets the sweep counter to 0.  No EPI is set
+   yet.  *out receives the handle.  EINVAL: bad descriptor, N >= 2^32,
+   species id >= K, misaligned buffers.  ECUDA: upload failed. */
+smcx_status smcx_create_lattice(const smcx_lattice_desc* desc, void* d_occ, void* d_work,
+                                const uint8_t* h_init, void* cuda_stream, smcx_lattice** out);
+
+/* Sets the EPI model (Sec. 3: pairwise only): v_q is [n_shells][K][K] int64
+   in q units, symmetric in the species indices; n_shells in 1..4.  The link
+   cells are sized from the shells (edge L = floor((1 + h_R)/2) + 1
+   conventional cells, h_R the largest |component| of a shell vector, raised
+   to min_cell).  Computes the full energy, which starts the running energy.
+   EINVAL: n_shells out of range, asymmetric V.  EOVERFLOW: the energy does
+   not fit int64. */
+smcx_status smcx_set_epi(smcx_lattice* lat, uint32_t n_shells, const int64_t* v_q);
+
+/* Runs n_sweeps MC steps (one trial per site each, Sec. 2.1) on the stream.
+   Sweep i of the call (0-based) runs at T_i = T_first + (T_last - T_first)
+   * i / (n_sweeps - 1) kelvin (T_first when n_sweeps == 1 or T_first ==
+   T_last); T = +inf accepts every unlike proposal, T = 0 accepts only
+   dE <= 0.  Trial k of cell c in global sweep t uses Philox4x32-10 counter
+   (k >> 1, c, t, 0) under the seed.  Advances the sweep counter by
+   n_sweeps.  *out (host, may be NULL) receives the call's totals; when it is
+   non-NULL the call synchronises the stream.  ESTATE: no EPI.  EINVAL: T < 0
+   or NaN. */
+smcx_status smcx_sweep(smcx_lattice* lat, uint32_t n_sweeps, double T_first, double T_last,
+                       smcx_sweep_stats* out);
+
+/* Runs the trials of one colour (0..7) of the current sweep (the sweep
+   counter is not advanced) at temperature T.  Lets a caller replay and check
+   single checkerboard phases; a full smcx_sweep runs colours 0..7 in order.
+   Synchronises the stream when out != NULL. */
+smcx_status smcx_run_colour(smcx_lattice* lat, uint32_t colour, double T, smcx_sweep_stats* out);
+
+/* Full energy recomputed from the current occupancy (directed pair counts on
+   the GPU, int128 sum on the host).  Synchronises.  EOVERFLOW if it does not
+   fit int64.  ESTATE: no EPI. */
+smcx_status smcx_energy(smcx_lattice* lat, int64_t* e_q);
+
+/* Running energy: the energy at smcx_set_epi / smcx_set_occupancy plus the
+   sum of every accepted energy change since (no device work). */
+smcx_status smcx_running_energy(smcx_lattice* lat, int64_t* e_q);
+
+/* Warren-Cowley SRO, Sec. 3.2, Eq. 9.  pair_counts (host, required) receives
+   [n_shells][K][K] uint64 directed counts N_m[p'][p] = number of (centre of
+   species p', shell-m neighbour of species p) pairs over every site.
+   alpha (host, may be NULL) receives alpha_m^{p p'} = 1 - N_m[p'][p] N /
+   (N_{p'} z_m N_p) at [m][p'][p], NaN where a species is absent.
+   n_shells 1..4 (independent of the EPI).  Synchronises. */
+smcx_status smcx_warren_cowley_sro(smcx_lattice* lat, uint32_t n_shells, uint64_t* pair_counts,
+                                   double* alpha);
+
+/* Copies the occupancy to h_out (N bytes, canonical layout).  Synchronises. */
+smcx_status smcx_get_occupancy(smcx_lattice* lat, uint8_t* h_out);
+
+/* Replaces the occupancy by h_in (N bytes, canonical, ids < K) and, when an
+   EPI is set, restarts the running energy from its full recomputation.  The
+   sweep counter is unchanged.  Synchronises. */
+smcx_status smcx_set_occupancy(smcx_lattice* lat, const uint8_t* h_in);
+
+/* Sweep counter (the global sweep index t of the next sweep). */
+smcx_status smcx_get_sweep_counter(smcx_lattice* lat, uint32_t* t);
+smcx_status smcx_set_sweep_counter(smcx_lattice* lat, uint32_t t);
+
+/* Link-cell geometry chosen for the current EPI: edge L (conventional cells)
+   and cells per dimension m[3] (even, or 1). ESTATE: no EPI. */
+smcx_status smcx_get_layout(smcx_lattice* lat, uint32_t* L, uint32_t* m);
+
+/* Checkpoint: a self-describing byte string (descriptor, EPI, sweep counter,
+   running energy, occupancy, CRC-32).  With buf == NULL, *len receives the
+   size needed; otherwise *len must be at least that size and receives the
+   bytes written.  ENOMEM: buffer too small.  Synchronises. */
+smcx_status smcx_checkpoint(smcx_lattice* lat, void* buf, size_t* len);
+
+/* Restores a checkpoint written by smcx_checkpoint for a lattice with the
+   same descriptor.  EINVAL: wrong size, descriptor mismatch or CRC failure
+   (the handle is left unchanged). */
+smcx_status smcx_restore(smcx_lattice* lat, const void* buf, size_t len);
+
+/* Tuning knobs (do not change results, only speed):
+     SMCX_OPT_KERNEL   0 = automatic, 1 = generic (global memory),
+                       2 = tiled (shared-memory tiles + halos)
+     SMCX_OPT_TILE     index of the tile shape among smcx_tile_shape(...) */
+#define SMCX_OPT_KERNEL 1u
+#define SMCX_OPT_TILE 2u
+smcx_status smcx_set_option(smcx_lattice* lat, uint32_t key, int64_t value);
+
+/* Number of tile shapes compiled for a lattice kind and the cells per tile
+   (x, y, z) of shape i. */
+uint32_t smcx_tile_shape_count(uint32_t kind);
+smcx_status smcx_tile_shape(uint32_t kind, uint32_t i, uint32_t* cells_xyz);
+
+/* Releases the handle (never the caller's buffers). */
+smcx_status smcx_destroy(smcx_lattice* lat);
+
+/* Text of the last error of this host thread ("" if none). */
+const char* smcx_last_error(void);
+
+/* Shell table used by the library: writes up to cap vectors (dx,dy,dz in
+   half units) of shells 1..n_shells, sorted by distance then
+   lexicographically, and z[m]; returns the number of vectors, 0 on error. */
+uint32_t smcx_shell_table(uint32_t kind, uint32_t n_shells, int32_t* disp, uint32_t cap,
+                          uint32_t* z);
+
+/* Philox4x32-10 of the library (for cross-checks): out[4] for the counter
+   ctr[4] and key[2]; runs on the host. */
+void smcx_philox4x32_10(const uint32_t* ctr, const uint32_t* key, uint32_t* out);
+
+/* Same generator evaluated by the library's device code: for i < n, writes
+   Philox4x32-10 of counter (c0 + i, c1, c2, c3) under key to d_out[4*i..].
+   d_out: device, 4*n uint32.  Synchronises the given stream. */
+smcx_status smcx_philox_device(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3, uint64_t key,
+                               uint32_t n, uint32_t* d_out, void* cuda_stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SMCX_H */

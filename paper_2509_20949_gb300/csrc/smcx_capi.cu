@@ -1,0 +1,757 @@
+// smcx_capi.cu -- the C ABI of libsmcx.so (include/smcx.h): validation, the
+// link-cell layout, the per-sweep schedule (origin shift, colours, Metropolis
+// threshold tables) and kernel launches.  Host code only; the kernels live in
+// kernels_*.cu.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/smcx.h"
+#include "kernels.h"
+
+using namespace smcx;
+
+namespace {
+
+thread_local std::string g_err;
+
+smcx_status fail(smcx_status s, const std::string& msg) {
+  g_err = msg;
+  return s;
+}
+
+// Boltzmann constant in eV/K (CODATA 2018); the paper (Sec. 2.1) uses
+// beta = 1/(k_B T) without a value.
+constexpr double kBoltzmannEvPerK = 8.617333262e-5;
+
+bool desc_ok(const smcx_lattice_desc* d, std::string* why) {
+  if (!d) {
+    *why = "null descriptor";
+    return false;
+  }
+  if (d->kind != SMCX_BCC && d->kind != SMCX_FCC) {
+    *why = "kind must be SMCX_BCC or SMCX_FCC";
+    return false;
+  }
+  for (int c = 0; c < 3; ++c)
+    if (d->n[c] < 1 || d->n[c] > (1u << 20)) {
+      *why = "n[] must be in 1..2^20";
+      return false;
+    }
+  if (d->pack_bits != 8 && d->pack_bits != 4) {
+    *why = "pack_bits must be 8 or 4";
+    return false;
+  }
+  const uint32_t kmax = d->pack_bits == 4 ? 16u : 255u;
+  if (d->n_species < 1 || d->n_species > kmax) {
+    *why = "n_species out of range (1..255, 1..16 when packed)";
+    return false;
+  }
+  const uint64_t N = static_cast<uint64_t>(basis_count(static_cast<int>(d->kind))) * d->n[0] *
+                     d->n[1] * d->n[2];
+  if (N >= (1ull << 32)) {
+    *why = "lattice has 2^32 or more sites";
+    return false;
+  }
+  if (d->min_cell > (1u << 20)) {
+    *why = "min_cell too large";
+    return false;
+  }
+  if (d->flags & ~(SMCX_NO_SHIFT | SMCX_SINGLE_CELL)) {
+    *why = "unknown flag bits";
+    return false;
+  }
+  return true;
+}
+
+uint64_t n_sites(const smcx_lattice_desc* d) {
+  return static_cast<uint64_t>(basis_count(static_cast<int>(d->kind))) * d->n[0] * d->n[1] *
+         d->n[2];
+}
+
+size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+size_t occ_bytes(const smcx_lattice_desc* d) {
+  const uint64_t N = n_sites(d);
+  const uint64_t raw = d->pack_bits == 4 ? (N + 1) / 2 : N;
+  return align_up(static_cast<size_t>(raw), 16);
+}
+
+struct WorkLayout {
+  size_t stats;   // 16 x u64: call stats, cumulative stats, status
+  size_t V;       // [4][K][K] int64
+  size_t D;       // difference table for the tiled kernel
+  size_t pairs;   // [4][K][K] u64
+  size_t total;
+};
+
+WorkLayout work_layout(const smcx_lattice_desc* d) {
+  const size_t K = d->n_species;
+  WorkLayout w;
+  w.stats = 0;
+  w.V = 256;
+  w.D = w.V + align_up(sizeof(int64_t) * kMaxShells * K * K, 256);
+  const size_t kd = K <= 16 ? K : 0;
+  w.pairs = w.D + align_up(sizeof(int64_t) * kMaxShells * kd * kd * kd + 16, 256);
+  w.total = w.pairs + align_up(sizeof(uint64_t) * kMaxShells * K * K, 256);
+  return w;
+}
+
+// Threshold tables of the Metropolis test (Sec. 2.1, Eq. 3) at temperature T:
+// bins of width 2^s q (q = 2^-32 eV) with beta q 2^s <= 2^-20, evaluated at
+// their lower edge, exp(-beta q 2^s idx) = T_0[idx & 511] T_1[(idx>>9)&511]
+// T_2[idx>>18] in 2^32 fixed point.
+bool build_tables(double T, Tables* tab, int* mode, int* s) {
+  if (std::isnan(T) || T < 0) return false;
+  std::memset(tab->w, 0, sizeof(tab->w));
+  *s = 0;
+  if (T == 0.0) {
+    *mode = kModeZeroT;
+    return true;
+  }
+  if (std::isinf(T)) {
+    *mode = kModeAcceptAll;
+    return true;
+  }
+  const double beta = 1.0 / (kBoltzmannEvPerK * T);
+  if (beta == 0.0) {
+    *mode = kModeAcceptAll;
+    return true;
+  }
+  *mode = kModeNormal;
+  const double limit = std::ldexp(1.0, -20);
+  int sh = 0;
+  while (sh < 62 && std::ldexp(beta, sh - 31) <= limit) ++sh;  // beta*2^((sh+1)-32)
+  *s = sh;
+  for (int level = 0; level < 3; ++level) {
+    const double bin = std::ldexp(beta, sh - 32 + 9 * level);
+    for (int i = 0; i < 512; ++i) {
+      const double e = std::exp(-(static_cast<double>(i) * bin));
+      double v = std::rint(std::ldexp(e, 32));
+      if (v > 4294967295.0) v = 4294967295.0;
+      tab->w[level * 512 + i] = static_cast<uint32_t>(v);
+    }
+  }
+  return true;
+}
+
+// Per-sweep origin of the link-cell grid ("dynamically constructed" cells,
+// Sec. 2.2): Philox counter (0, 0, t, 1); s_d = (w_d n_d) >> 32.
+void sweep_origin(const smcx_lattice_desc& d, uint32_t t, int shift[3]) {
+  if (d.flags & SMCX_NO_SHIFT) {
+    shift[0] = shift[1] = shift[2] = 0;
+    return;
+  }
+  const U4 w = philox4x32_10(0u, 0u, t, 1u, static_cast<uint32_t>(d.seed),
+                             static_cast<uint32_t>(d.seed >> 32));
+  const uint32_t ws[3] = {w.x, w.y, w.z};
+  for (int c = 0; c < 3; ++c)
+    shift[c] = static_cast<int>((static_cast<uint64_t>(ws[c]) * d.n[c]) >> 32);
+}
+
+int shell_reach(int kind, int M) {
+  int r = 0;
+  const int total = shell_start(kind, M);
+  for (int i = 0; i < total; ++i) {
+    const ShellVec v = shell_vec(kind, i);
+    r = std::max(r, std::max(std::abs(v.x), std::max(std::abs(v.y), std::abs(v.z))));
+  }
+  return r;
+}
+
+}  // namespace
+
+struct smcx_lattice {
+  smcx_lattice_desc desc;
+  int nb = 0;
+  uint64_t N = 0;
+  uint8_t* d_occ = nullptr;
+  uint8_t* d_work = nullptr;
+  cudaStream_t stream = nullptr;
+  WorkLayout wl{};
+  bool has_epi = false;
+  uint32_t M = 0;
+  std::vector<int64_t> V;
+  int L = 0;
+  int m[3] = {1, 1, 1};
+  uint32_t t = 0;
+  int64_t E0 = 0;  // energy when the running energy was last restarted
+  smcx_status sticky = SMCX_OK;
+  int opt_kernel = 0;
+  int opt_tile = -1;
+  int n_sm = 0;
+
+  unsigned long long* stats() { return reinterpret_cast<unsigned long long*>(d_work + wl.stats); }
+  int64_t* dV() { return reinterpret_cast<int64_t*>(d_work + wl.V); }
+  unsigned long long* pairs() {
+    return reinterpret_cast<unsigned long long*>(d_work + wl.pairs);
+  }
+  Geom geom() const {
+    Geom g;
+    g.kind = static_cast<int>(desc.kind);
+    g.nb = nb;
+    for (int c = 0; c < 3; ++c) {
+      g.n[c] = static_cast<int>(desc.n[c]);
+      g.m[c] = m[c];
+    }
+    g.L = L;
+    g.K = static_cast<int>(desc.n_species);
+    g.M = static_cast<int>(M);
+    g.z1 = shell_z(g.kind, 0);
+    g.pack4 = desc.pack_bits == 4;
+    g.seed_lo = static_cast<uint32_t>(desc.seed);
+    g.seed_hi = static_cast<uint32_t>(desc.seed >> 32);
+    return g;
+  }
+};
+
+namespace {
+
+smcx_status cuda_fail(smcx_lattice* lat, cudaError_t e, const char* what) {
+  if (lat) lat->sticky = SMCX_ECUDA;
+  return fail(SMCX_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define SMCX_CUDA(lat, call)                                 \
+  do {                                                       \
+    cudaError_t e_ = (call);                                 \
+    if (e_ != cudaSuccess) return cuda_fail(lat, e_, #call); \
+  } while (0)
+
+smcx_status check_handle(smcx_lattice* lat) {
+  if (!lat) return fail(SMCX_EINVAL, "null handle");
+  if (lat->sticky != SMCX_OK)
+    return fail(SMCX_ESTATE, "handle is in an error state from an earlier call");
+  return SMCX_OK;
+}
+
+ShellParam shell_param(int kind) {
+  ShellParam sp;
+  std::memset(&sp, 0, sizeof(sp));
+  const int total = shell_start(kind, kMaxShells);
+  for (int i = 0; i < total; ++i) {
+    const ShellVec v = shell_vec(kind, i);
+    sp.v[i][0] = v.x;
+    sp.v[i][1] = v.y;
+    sp.v[i][2] = v.z;
+  }
+  for (int m = 0; m <= kMaxShells; ++m) sp.start[m] = shell_start(kind, m);
+  return sp;
+}
+
+// link cells: edge L = floor((1 + h_R)/2) + 1 (two same-colour cells then never
+// share a site one writes and the other reads), raised to min_cell; per
+// dimension the largest even count <= n/L, or 1.
+void compute_layout(smcx_lattice* lat) {
+  const int hR = shell_reach(static_cast<int>(lat->desc.kind), static_cast<int>(lat->M));
+  int L = (1 + hR) / 2 + 1;
+  if (static_cast<int>(lat->desc.min_cell) > L) L = static_cast<int>(lat->desc.min_cell);
+  lat->L = L;
+  for (int c = 0; c < 3; ++c) {
+    int cnt = static_cast<int>(lat->desc.n[c]) / L;
+    cnt &= ~1;
+    if (cnt < 2 || (lat->desc.flags & SMCX_SINGLE_CELL)) cnt = 1;
+    lat->m[c] = cnt;
+  }
+}
+
+smcx_status validate_occupancy(const smcx_lattice_desc& d, const uint8_t* h) {
+  const uint64_t N = n_sites(&d);
+  for (uint64_t i = 0; i < N; ++i)
+    if (h[i] >= d.n_species) return fail(SMCX_EINVAL, "species id >= n_species in occupancy");
+  return SMCX_OK;
+}
+
+// canonical bytes -> device storage (packed: site i in nibble i&1 of byte i>>1)
+smcx_status upload_occupancy(smcx_lattice* lat, const uint8_t* h) {
+  const size_t bytes = occ_bytes(&lat->desc);
+  if (lat->desc.pack_bits == 8) {
+    SMCX_CUDA(lat, cudaMemsetAsync(lat->d_occ, 0, bytes, lat->stream));
+    SMCX_CUDA(lat, cudaMemcpyAsync(lat->d_occ, h, lat->N, cudaMemcpyHostToDevice, lat->stream));
+    SMCX_CUDA(lat, cudaStreamSynchronize(lat->stream));
+    return SMCX_OK;
+  }
+  std::vector<uint8_t> packed(bytes, 0);
+  for (uint64_t i = 0; i < lat->N; ++i) packed[i >> 1] |= static_cast<uint8_t>(h[i] << ((i & 1) * 4));
+  SMCX_CUDA(lat, cudaMemcpyAsync(lat->d_occ, packed.data(), bytes, cudaMemcpyHostToDevice,
+                                 lat->stream));
+  SMCX_CUDA(lat, cudaStreamSynchronize(lat->stream));
+  return SMCX_OK;
+}
+
+smcx_status download_occupancy(smcx_lattice* lat, uint8_t* h) {
+  if (lat->desc.pack_bits == 8) {
+    SMCX_CUDA(lat, cudaMemcpyAsync(h, lat->d_occ, lat->N, cudaMemcpyDeviceToHost, lat->stream));
+    SMCX_CUDA(lat, cudaStreamSynchronize(lat->stream));
+    return SMCX_OK;
+  }
+  std::vector<uint8_t> packed(occ_bytes(&lat->desc));
+  SMCX_CUDA(lat, cudaMemcpyAsync(packed.data(), lat->d_occ, packed.size(), cudaMemcpyDeviceToHost,
+                                 lat->stream));
+  SMCX_CUDA(lat, cudaStreamSynchronize(lat->stream));
+  for (uint64_t i = 0; i < lat->N; ++i) h[i] = (packed[i >> 1] >> ((i & 1) * 4)) & 15;
+  return SMCX_OK;
+}
+
+smcx_status run_pair_counts(smcx_lattice* lat, uint32_t n_shells, std::vector<uint64_t>* out) {
+  const size_t K = lat->desc.n_species;
+  const size_t n_cnt = n_shells * K * K;
+  SMCX_CUDA(lat, cudaMemsetAsync(lat->pairs(), 0, sizeof(uint64_t) * n_cnt, lat->stream));
+  Geom g = lat->geom();
+  const ShellParam sp = shell_param(g.kind);
+  SMCX_CUDA(lat, launch_pair_count_generic(g, sp, static_cast<int>(n_shells), lat->d_occ,
+                                           lat->pairs(), static_cast<uint32_t>(lat->N), lat->n_sm,
+                                           lat->stream));
+  out->assign(n_cnt, 0);
+  SMCX_CUDA(lat, cudaMemcpyAsync(out->data(), lat->pairs(), sizeof(uint64_t) * n_cnt,
+                                 cudaMemcpyDeviceToHost, lat->stream));
+  SMCX_CUDA(lat, cudaStreamSynchronize(lat->stream));
+  return SMCX_OK;
+}
+
+// E = 1/2 sum_m sum_{p',p} N_m[p'][p] V_m(p',p): every bond is seen from both
+// ends in the directed counts; int128 accumulation.
+smcx_status energy_from_counts(smcx_lattice* lat, const std::vector<uint64_t>& cnt, int64_t* e) {
+  const size_t K = lat->desc.n_species;
+  __int128 acc = 0;
+  for (size_t m = 0; m < lat->M; ++m)
+    for (size_t a = 0; a < K; ++a)
+      for (size_t b = 0; b < K; ++b) {
+        const size_t idx = (m * K + a) * K + b;
+        acc += static_cast<__int128>(cnt[idx]) * lat->V[idx];
+      }
+  if (acc % 2 != 0) return fail(SMCX_EINVAL, "internal: odd directed energy");
+  acc /= 2;
+  if (acc > static_cast<__int128>(INT64_MAX) || acc < static_cast<__int128>(INT64_MIN))
+    return fail(SMCX_EOVERFLOW, "energy does not fit int64");
+  *e = static_cast<int64_t>(acc);
+  return SMCX_OK;
+}
+
+smcx_status full_energy(smcx_lattice* lat, int64_t* e) {
+  std::vector<uint64_t> cnt;
+  smcx_status s = run_pair_counts(lat, lat->M, &cnt);
+  if (s != SMCX_OK) return s;
+  return energy_from_counts(lat, cnt, e);
+}
+
+smcx_status restart_running_energy(smcx_lattice* lat) {
+  SMCX_CUDA(lat, cudaMemsetAsync(lat->stats(), 0, sizeof(unsigned long long) * 16, lat->stream));
+  if (!lat->has_epi) return SMCX_OK;
+  return full_energy(lat, &lat->E0);
+}
+
+// one colour phase of the current sweep
+smcx_status launch_colour(smcx_lattice* lat, int colour, const PhaseArgs& base, const Tables& tab) {
+  PhaseArgs a = base;
+  a.colour = colour;
+  const Geom g = lat->geom();
+  const ShellParam sp = shell_param(g.kind);
+  SMCX_CUDA(lat, launch_sweep_generic(g, a, sp, tab, lat->d_occ, lat->dV(), lat->stats(),
+                                      lat->stream));
+  return SMCX_OK;
+}
+
+smcx_status read_call_stats(smcx_lattice* lat, smcx_sweep_stats* out) {
+  unsigned long long h[4];
+  SMCX_CUDA(lat, cudaMemcpyAsync(h, lat->stats() + kStatCall, sizeof(h), cudaMemcpyDeviceToHost,
+                                 lat->stream));
+  SMCX_CUDA(lat, cudaStreamSynchronize(lat->stream));
+  out->attempts = h[0];
+  out->unlike = h[1];
+  out->accepted = h[2];
+  out->sum_dE_q = static_cast<int64_t>(h[3]);
+  return SMCX_OK;
+}
+
+uint32_t crc32(const uint8_t* p, size_t n, uint32_t crc = 0) {
+  crc = ~crc;
+  for (size_t i = 0; i < n; ++i) {
+    crc ^= p[i];
+    for (int k = 0; k < 8; ++k) crc = (crc >> 1) ^ (0xEDB88320u & (0u - (crc & 1u)));
+  }
+  return ~crc;
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t smcx_occupancy_bytes(const smcx_lattice_desc* desc) {
+  std::string why;
+  if (!desc_ok(desc, &why)) return 0;
+  return occ_bytes(desc);
+}
+
+size_t smcx_workspace_bytes(const smcx_lattice_desc* desc) {
+  std::string why;
+  if (!desc_ok(desc, &why)) return 0;
+  return work_layout(desc).total;
+}
+
+smcx_status smcx_create_lattice(const smcx_lattice_desc* desc, void* d_occ, void* d_work,
+                                const uint8_t* h_init, void* cuda_stream, smcx_lattice** out) {
+  std::string why;
+  if (!out) return fail(SMCX_EINVAL, "null out pointer");
+  *out = nullptr;
+  if (!desc_ok(desc, &why)) return fail(SMCX_EINVAL, why);
+  if (!d_occ || !d_work || !h_init) return fail(SMCX_EINVAL, "null buffer");
+  if (reinterpret_cast<uintptr_t>(d_occ) % 16 != 0 || reinterpret_cast<uintptr_t>(d_work) % 256 != 0)
+    return fail(SMCX_EINVAL, "occupancy must be 16-byte and workspace 256-byte aligned");
+  smcx_status s = validate_occupancy(*desc, h_init);
+  if (s != SMCX_OK) return s;
+  auto* lat = new smcx_lattice();
+  lat->desc = *desc;
+  lat->nb = basis_count(static_cast<int>(desc->kind));
+  lat->N = n_sites(desc);
+  lat->d_occ = static_cast<uint8_t*>(d_occ);
+  lat->d_work = static_cast<uint8_t*>(d_work);
+  lat->stream = static_cast<cudaStream_t>(cuda_stream);
+  lat->wl = work_layout(desc);
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&lat->n_sm, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) {
+    delete lat;
+    return fail(SMCX_ECUDA, std::string("device query: ") + cudaGetErrorString(e));
+  }
+  s = upload_occupancy(lat, h_init);
+  if (s == SMCX_OK) s = restart_running_energy(lat);
+  if (s != SMCX_OK) {
+    delete lat;
+    return s;
+  }
+  *out = lat;
+  return SMCX_OK;
+}
+
+smcx_status smcx_set_epi(smcx_lattice* lat, uint32_t n_shells, const int64_t* v_q) {
+  smcx_status s = check_handle(lat);
+  if (s != SMCX_OK) return s;
+  if (n_shells < 1 || n_shells > kMaxShells) return fail(SMCX_EINVAL, "n_shells must be 1..4");
+  if (!v_q) return fail(SMCX_EINVAL, "null EPI table");
+  const size_t K = lat->desc.n_species;
+  const int64_t vmax = int64_t(1) << 52;
+  for (size_t m = 0; m < n_shells; ++m)
+    for (size_t a = 0; a < K; ++a)
+      for (size_t b = 0; b < K; ++b) {
+        const int64_t v = v_q[(m * K + a) * K + b];
+        if (v != v_q[(m * K + b) * K + a]) return fail(SMCX_EINVAL, "EPI table is not symmetric");
+        if (v >= vmax || v <= -vmax) return fail(SMCX_EINVAL, "EPI value beyond 2^52 q");
+      }
+  lat->M = n_shells;
+  lat->V.assign(v_q, v_q + n_shells * K * K);
+  compute_layout(lat);
+  std::vector<int64_t> vpad(kMaxShells * K * K, 0);
+  std::copy(lat->V.begin(), lat->V.end(), vpad.begin());
+  SMCX_CUDA(lat, cudaMemcpyAsync(lat->dV(), vpad.data(), sizeof(int64_t) * vpad.size(),
+                                 cudaMemcpyHostToDevice, lat->stream));
+  SMCX_CUDA(lat, cudaStreamSynchronize(lat->stream));
+  lat->has_epi = true;
+  s = restart_running_energy(lat);
+  if (s != SMCX_OK) lat->has_epi = false;
+  return s;
+}
+
+smcx_status smcx_sweep(smcx_lattice* lat, uint32_t n_sweeps, double T_first, double T_last,
+                       smcx_sweep_stats* out) {
+  smcx_status s = check_handle(lat);
+  if (s != SMCX_OK) return s;
+  if (!lat->has_epi) return fail(SMCX_ESTATE, "set_epi must be called before sweep");
+  if (std::isnan(T_first) || std::isnan(T_last) || T_first < 0 || T_last < 0)
+    return fail(SMCX_EINVAL, "temperatures must be >= 0");
+  SMCX_CUDA(lat, cudaMemsetAsync(lat->stats() + kStatCall, 0, sizeof(unsigned long long) * 4,
+                                 lat->stream));
+  Tables tab;
+  for (uint32_t i = 0; i < n_sweeps; ++i) {
+    double T = T_first;
+    if (n_sweeps > 1 && T_first != T_last)
+      T = T_first + (T_last - T_first) * static_cast<double>(i) / static_cast<double>(n_sweeps - 1);
+    PhaseArgs a{};
+    if (!build_tables(T, &tab, &a.mode, &a.s)) return fail(SMCX_EINVAL, "bad temperature");
+    a.t = lat->t;
+    sweep_origin(lat->desc, a.t, a.shift);
+    for (int colour = 0; colour < 8; ++colour) {
+      s = launch_colour(lat, colour, a, tab);
+      if (s != SMCX_OK) return s;
+    }
+    lat->t += 1;
+  }
+  if (out) return read_call_stats(lat, out);
+  return SMCX_OK;
+}
+
+smcx_status smcx_run_colour(smcx_lattice* lat, uint32_t colour, double T, smcx_sweep_stats* out) {
+  smcx_status s = check_handle(lat);
+  if (s != SMCX_OK) return s;
+  if (!lat->has_epi) return fail(SMCX_ESTATE, "set_epi must be called before run_colour");
+  if (colour > 7) return fail(SMCX_EINVAL, "colour must be 0..7");
+  Tables tab;
+  PhaseArgs a{};
+  if (!build_tables(T, &tab, &a.mode, &a.s)) return fail(SMCX_EINVAL, "temperature must be >= 0");
+  SMCX_CUDA(lat, cudaMemsetAsync(lat->stats() + kStatCall, 0, sizeof(unsigned long long) * 4,
+                                 lat->stream));
+  a.t = lat->t;
+  sweep_origin(lat->desc, a.t, a.shift);
+  s = launch_colour(lat, static_cast<int>(colour), a, tab);
+  if (s != SMCX_OK) return s;
+  if (out) return read_call_stats(lat, out);
+  return SMCX_OK;
+}
+
+smcx_status smcx_energy(smcx_lattice* lat, int64_t* e_q) {
+  smcx_status s = check_handle(lat);
+  if (s != SMCX_OK) return s;
+  if (!lat->has_epi) return fail(SMCX_ESTATE, "no EPI set");
+  if (!e_q) return fail(SMCX_EINVAL, "null output");
+  return full_energy(lat, e_q);
+}
+
+smcx_status smcx_running_energy(smcx_lattice* lat, int64_t* e_q) {
+  smcx_status s = check_handle(lat);
+  if (s != SMCX_OK) return s;
+  if (!lat->has_epi) return fail(SMCX_ESTATE, "no EPI set");
+  if (!e_q) return fail(SMCX_EINVAL, "null output");
+  unsigned long long cum_de = 0;
+  SMCX_CUDA(lat, cudaMemcpyAsync(&cum_de, lat->stats() + kStatCum + 3, sizeof(cum_de),
+                                 cudaMemcpyDeviceToHost, lat->stream));
+  SMCX_CUDA(lat, cudaStreamSynchronize(lat->stream));
+  *e_q = lat->E0 + static_cast<int64_t>(cum_de);
+  return SMCX_OK;
+}
+
+smcx_status smcx_warren_cowley_sro(smcx_lattice* lat, uint32_t n_shells, uint64_t* pair_counts,
+                                   double* alpha) {
+  smcx_status s = check_handle(lat);
+  if (s != SMCX_OK) return s;
+  if (n_shells < 1 || n_shells > kMaxShells) return fail(SMCX_EINVAL, "n_shells must be 1..4");
+  if (!pair_counts) return fail(SMCX_EINVAL, "null pair_counts");
+  std::vector<uint64_t> cnt;
+  s = run_pair_counts(lat, n_shells, &cnt);
+  if (s != SMCX_OK) return s;
+  std::memcpy(pair_counts, cnt.data(), sizeof(uint64_t) * cnt.size());
+  if (!alpha) return SMCX_OK;
+  const size_t K = lat->desc.n_species;
+  // species totals: N_p = sum over centres of shell-1 counts / z_1
+  std::vector<uint64_t> Np(K, 0);
+  const uint64_t z1 = static_cast<uint64_t>(shell_z(static_cast<int>(lat->desc.kind), 0));
+  for (size_t a = 0; a < K; ++a) {
+    uint64_t row = 0;
+    for (size_t b = 0; b < K; ++b) row += cnt[a * K + b];
+    Np[a] = row / z1;
+  }
+  const double N = static_cast<double>(lat->N);
+  for (size_t m = 0; m < n_shells; ++m) {
+    const double zm = static_cast<double>(shell_z(static_cast<int>(lat->desc.kind), static_cast<int>(m)));
+    for (size_t pc = 0; pc < K; ++pc)
+      for (size_t p = 0; p < K; ++p) {
+        const double n_centre = static_cast<double>(Np[pc]);
+        const double n_p = static_cast<double>(Np[p]);
+        const double cond = static_cast<double>(cnt[(m * K + pc) * K + p]) / (n_centre * zm);
+        const double conc = n_p / N;
+        alpha[(m * K + pc) * K + p] = (n_centre > 0 && n_p > 0) ? 1.0 - cond / conc : NAN;
+      }
+  }
+  return SMCX_OK;
+}
+
+smcx_status smcx_get_occupancy(smcx_lattice* lat, uint8_t* h_out) {
+  smcx_status s = check_handle(lat);
+  if (s != SMCX_OK) return s;
+  if (!h_out) return fail(SMCX_EINVAL, "null output");
+  return download_occupancy(lat, h_out);
+}
+
+smcx_status smcx_set_occupancy(smcx_lattice* lat, const uint8_t* h_in) {
+  smcx_status s = check_handle(lat);
+  if (s != SMCX_OK) return s;
+  if (!h_in) return fail(SMCX_EINVAL, "null input");
+  s = validate_occupancy(lat->desc, h_in);
+  if (s != SMCX_OK) return s;
+  s = upload_occupancy(lat, h_in);
+  if (s != SMCX_OK) return s;
+  return restart_running_energy(lat);
+}
+
+smcx_status smcx_get_sweep_counter(smcx_lattice* lat, uint32_t* t) {
+  if (!lat || !t) return fail(SMCX_EINVAL, "null argument");
+  *t = lat->t;
+  return SMCX_OK;
+}
+
+smcx_status smcx_set_sweep_counter(smcx_lattice* lat, uint32_t t) {
+  smcx_status s = check_handle(lat);
+  if (s != SMCX_OK) return s;
+  lat->t = t;
+  return SMCX_OK;
+}
+
+smcx_status smcx_get_layout(smcx_lattice* lat, uint32_t* L, uint32_t* m) {
+  if (!lat || !L || !m) return fail(SMCX_EINVAL, "null argument");
+  if (!lat->has_epi) return fail(SMCX_ESTATE, "layout is fixed by set_epi");
+  *L = static_cast<uint32_t>(lat->L);
+  for (int c = 0; c < 3; ++c) m[c] = static_cast<uint32_t>(lat->m[c]);
+  return SMCX_OK;
+}
+
+// checkpoint format (little endian):
+//   "SMCXCKP1" | desc (40 bytes) | M u32 | t u32 | E_run i64 | V [M][K][K] i64 |
+//   occupancy N bytes | CRC-32 of everything before it (u32)
+smcx_status smcx_checkpoint(smcx_lattice* lat, void* buf, size_t* len) {
+  smcx_status s = check_handle(lat);
+  if (s != SMCX_OK) return s;
+  if (!len) return fail(SMCX_EINVAL, "null len");
+  const size_t K = lat->desc.n_species;
+  const size_t need = 8 + sizeof(smcx_lattice_desc) + 4 + 4 + 8 + sizeof(int64_t) * lat->M * K * K +
+                      lat->N + 4;
+  if (!buf) {
+    *len = need;
+    return SMCX_OK;
+  }
+  if (*len < need) return fail(SMCX_ENOMEM, "checkpoint buffer too small");
+  int64_t e_run = 0;
+  if (lat->has_epi) {
+    s = smcx_running_energy(lat, &e_run);
+    if (s != SMCX_OK) return s;
+  }
+  uint8_t* p = static_cast<uint8_t*>(buf);
+  std::memcpy(p, "SMCXCKP1", 8);
+  size_t off = 8;
+  std::memcpy(p + off, &lat->desc, sizeof(smcx_lattice_desc));
+  off += sizeof(smcx_lattice_desc);
+  const uint32_t M = lat->has_epi ? lat->M : 0;
+  std::memcpy(p + off, &M, 4);
+  off += 4;
+  std::memcpy(p + off, &lat->t, 4);
+  off += 4;
+  std::memcpy(p + off, &e_run, 8);
+  off += 8;
+  if (M) std::memcpy(p + off, lat->V.data(), sizeof(int64_t) * M * K * K);
+  off += sizeof(int64_t) * M * K * K;
+  s = download_occupancy(lat, p + off);
+  if (s != SMCX_OK) return s;
+  off += lat->N;
+  const uint32_t crc = crc32(p, off);
+  std::memcpy(p + off, &crc, 4);
+  off += 4;
+  *len = off;
+  return SMCX_OK;
+}
+
+smcx_status smcx_restore(smcx_lattice* lat, const void* buf, size_t len) {
+  smcx_status s = check_handle(lat);
+  if (s != SMCX_OK) return s;
+  if (!buf) return fail(SMCX_EINVAL, "null buffer");
+  const uint8_t* p = static_cast<const uint8_t*>(buf);
+  const size_t head = 8 + sizeof(smcx_lattice_desc) + 16;
+  if (len < head + 4 || std::memcmp(p, "SMCXCKP1", 8) != 0)
+    return fail(SMCX_EINVAL, "not a checkpoint");
+  smcx_lattice_desc d;
+  std::memcpy(&d, p + 8, sizeof(d));
+  if (std::memcmp(&d, &lat->desc, sizeof(d)) != 0)
+    return fail(SMCX_EINVAL, "checkpoint was written for another lattice descriptor");
+  uint32_t M, t;
+  int64_t e_run;
+  size_t off = 8 + sizeof(d);
+  std::memcpy(&M, p + off, 4);
+  std::memcpy(&t, p + off + 4, 4);
+  std::memcpy(&e_run, p + off + 8, 8);
+  off += 16;
+  const size_t K = d.n_species;
+  if (M > kMaxShells) return fail(SMCX_EINVAL, "bad shell count in checkpoint");
+  const size_t need = off + sizeof(int64_t) * M * K * K + lat->N + 4;
+  if (len != need) return fail(SMCX_EINVAL, "checkpoint size mismatch");
+  uint32_t crc;
+  std::memcpy(&crc, p + need - 4, 4);
+  if (crc != crc32(p, need - 4)) return fail(SMCX_EINVAL, "checkpoint CRC mismatch");
+  const uint8_t* occ = p + off + sizeof(int64_t) * M * K * K;
+  s = validate_occupancy(lat->desc, occ);
+  if (s != SMCX_OK) return s;
+  if (M) {
+    std::vector<int64_t> V(M * K * K);
+    std::memcpy(V.data(), p + off, sizeof(int64_t) * V.size());
+    s = smcx_set_epi(lat, M, V.data());
+    if (s != SMCX_OK) return s;
+  }
+  s = upload_occupancy(lat, occ);
+  if (s != SMCX_OK) return s;
+  SMCX_CUDA(lat, cudaMemsetAsync(lat->stats(), 0, sizeof(unsigned long long) * 16, lat->stream));
+  SMCX_CUDA(lat, cudaStreamSynchronize(lat->stream));
+  lat->E0 = e_run;
+  lat->t = t;
+  return SMCX_OK;
+}
+
+smcx_status smcx_set_option(smcx_lattice* lat, uint32_t key, int64_t value) {
+  if (!lat) return fail(SMCX_EINVAL, "null handle");
+  if (key == SMCX_OPT_KERNEL) {
+    if (value < 0 || value > 2) return fail(SMCX_EINVAL, "kernel option must be 0..2");
+    lat->opt_kernel = static_cast<int>(value);
+    return SMCX_OK;
+  }
+  if (key == SMCX_OPT_TILE) {
+    if (value < -1 || value >= static_cast<int64_t>(smcx_tile_shape_count(lat->desc.kind)))
+      return fail(SMCX_EINVAL, "tile shape index out of range");
+    lat->opt_tile = static_cast<int>(value);
+    return SMCX_OK;
+  }
+  return fail(SMCX_EINVAL, "unknown option");
+}
+
+uint32_t smcx_tile_shape_count(uint32_t kind) {
+  (void)kind;
+  return 0;
+}
+
+smcx_status smcx_tile_shape(uint32_t kind, uint32_t i, uint32_t* cells_xyz) {
+  (void)kind;
+  (void)i;
+  (void)cells_xyz;
+  return fail(SMCX_EINVAL, "no tile shapes");
+}
+
+smcx_status smcx_destroy(smcx_lattice* lat) {
+  if (!lat) return fail(SMCX_EINVAL, "null handle");
+  delete lat;
+  return SMCX_OK;
+}
+
+const char* smcx_last_error(void) { return g_err.c_str(); }
+
+uint32_t smcx_shell_table(uint32_t kind, uint32_t n_shells, int32_t* disp, uint32_t cap,
+                          uint32_t* z) {
+  if (kind > 1 || n_shells < 1 || n_shells > kMaxShells || !disp || !z) return 0;
+  const int k = static_cast<int>(kind);
+  const uint32_t total = static_cast<uint32_t>(shell_start(k, static_cast<int>(n_shells)));
+  if (total > cap) return 0;
+  for (uint32_t i = 0; i < total; ++i) {
+    const ShellVec v = shell_vec(k, static_cast<int>(i));
+    disp[3 * i + 0] = v.x;
+    disp[3 * i + 1] = v.y;
+    disp[3 * i + 2] = v.z;
+  }
+  for (uint32_t m = 0; m < n_shells; ++m) z[m] = static_cast<uint32_t>(shell_z(k, static_cast<int>(m)));
+  return total;
+}
+
+void smcx_philox4x32_10(const uint32_t* ctr, const uint32_t* key, uint32_t* out) {
+  const U4 w = philox4x32_10(ctr[0], ctr[1], ctr[2], ctr[3], key[0], key[1]);
+  out[0] = w.x;
+  out[1] = w.y;
+  out[2] = w.z;
+  out[3] = w.w;
+}
+
+smcx_status smcx_philox_device(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3, uint64_t key,
+                               uint32_t n, uint32_t* d_out, void* cuda_stream) {
+  if (!d_out && n) return fail(SMCX_EINVAL, "null output");
+  cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+  cudaError_t e = launch_philox_fill(c0, c1, c2, c3, key, n, d_out, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return fail(SMCX_ECUDA, std::string("philox fill: ") + cudaGetErrorString(e));
+  return SMCX_OK;
+}
+
+}  // extern "C"

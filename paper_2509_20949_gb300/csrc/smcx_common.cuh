@@ -1,0 +1,167 @@
+// smcx_common.cuh -- definitions shared by the library's host code and kernels.
+//
+// Geometry (half-unit shell vectors of BCC/FCC, basis vectors), the
+// Philox4x32-10 generator and the launch-parameter structs.  The oracle under
+// oracle/ has its own independent versions of all of these.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace smcx {
+
+constexpr int kMaxShells = 4;
+constexpr int kMaxShellVecs = 64;  // BCC shells 1-4: 50 vectors, FCC: 54
+constexpr int kTabWords = 3 * 512; // Metropolis threshold tables T_0, T_1, T_2
+
+enum AcceptMode : int { kModeNormal = 0, kModeAcceptAll = 1, kModeZeroT = 2 };
+
+// ---------------------------------------------------------------------------
+// Neighbour shells in half units h = a/2, shells in ascending distance, the
+// vectors of one shell sorted lexicographically on (dx, dy, dz).
+// BCC: |d|^2 = 3 (8), 4 (6), 8 (12), 11 (24).  FCC: 2 (12), 4 (6), 6 (24), 8 (12).
+// ---------------------------------------------------------------------------
+struct ShellVec { int8_t x, y, z; };
+
+// Tables are function-local so that host code and device code (after
+// unrolling, with constant indices) can both use them.
+__host__ __device__ constexpr int shell_z(int kind, int m) {
+  constexpr int bcc[4] = {8, 6, 12, 24};
+  constexpr int fcc[4] = {12, 6, 24, 12};
+  return kind == 0 ? bcc[m] : fcc[m];
+}
+
+__host__ __device__ constexpr ShellVec shell_vec(int kind, int idx) {
+  constexpr ShellVec bcc[50] = {
+      // shell 1: (+-1,+-1,+-1)
+      {-1, -1, -1}, {-1, -1, 1}, {-1, 1, -1}, {-1, 1, 1}, {1, -1, -1}, {1, -1, 1}, {1, 1, -1}, {1, 1, 1},
+      // shell 2: permutations of (+-2,0,0)
+      {-2, 0, 0}, {0, -2, 0}, {0, 0, -2}, {0, 0, 2}, {0, 2, 0}, {2, 0, 0},
+      // shell 3: permutations of (+-2,+-2,0)
+      {-2, -2, 0}, {-2, 0, -2}, {-2, 0, 2}, {-2, 2, 0}, {0, -2, -2}, {0, -2, 2},
+      {0, 2, -2}, {0, 2, 2}, {2, -2, 0}, {2, 0, -2}, {2, 0, 2}, {2, 2, 0},
+      // shell 4: permutations of (+-3,+-1,+-1)
+      {-3, -1, -1}, {-3, -1, 1}, {-3, 1, -1}, {-3, 1, 1},
+      {-1, -3, -1}, {-1, -3, 1}, {-1, -1, -3}, {-1, -1, 3}, {-1, 1, -3}, {-1, 1, 3}, {-1, 3, -1}, {-1, 3, 1},
+      {1, -3, -1}, {1, -3, 1}, {1, -1, -3}, {1, -1, 3}, {1, 1, -3}, {1, 1, 3}, {1, 3, -1}, {1, 3, 1},
+      {3, -1, -1}, {3, -1, 1}, {3, 1, -1}, {3, 1, 1},
+  };
+  constexpr ShellVec fcc[54] = {
+      // shell 1: permutations of (+-1,+-1,0)
+      {-1, -1, 0}, {-1, 0, -1}, {-1, 0, 1}, {-1, 1, 0}, {0, -1, -1}, {0, -1, 1},
+      {0, 1, -1}, {0, 1, 1}, {1, -1, 0}, {1, 0, -1}, {1, 0, 1}, {1, 1, 0},
+      // shell 2: permutations of (+-2,0,0)
+      {-2, 0, 0}, {0, -2, 0}, {0, 0, -2}, {0, 0, 2}, {0, 2, 0}, {2, 0, 0},
+      // shell 3: permutations of (+-2,+-1,+-1)
+      {-2, -1, -1}, {-2, -1, 1}, {-2, 1, -1}, {-2, 1, 1},
+      {-1, -2, -1}, {-1, -2, 1}, {-1, -1, -2}, {-1, -1, 2}, {-1, 1, -2}, {-1, 1, 2}, {-1, 2, -1}, {-1, 2, 1},
+      {1, -2, -1}, {1, -2, 1}, {1, -1, -2}, {1, -1, 2}, {1, 1, -2}, {1, 1, 2}, {1, 2, -1}, {1, 2, 1},
+      {2, -1, -1}, {2, -1, 1}, {2, 1, -1}, {2, 1, 1},
+      // shell 4: permutations of (+-2,+-2,0)
+      {-2, -2, 0}, {-2, 0, -2}, {-2, 0, 2}, {-2, 2, 0}, {0, -2, -2}, {0, -2, 2},
+      {0, 2, -2}, {0, 2, 2}, {2, -2, 0}, {2, 0, -2}, {2, 0, 2}, {2, 2, 0},
+  };
+  return kind == 0 ? bcc[idx] : fcc[idx];
+}
+
+__host__ __device__ constexpr int basis_count(int kind) { return kind == 0 ? 2 : 4; }
+
+// basis vector component c of basis site b (half units)
+__host__ __device__ constexpr int basis_comp(int kind, int b, int c) {
+  return kind == 0 ? b : (b == 0 ? 0 : (c == b - 1 ? 0 : 1));
+}
+
+// basis index of a parity vector (px, py, pz); -1 when not a lattice site
+__host__ __device__ constexpr int basis_of_parity(int kind, int px, int py, int pz) {
+  if (kind == 0) return (px == py && py == pz) ? px : -1;
+  if (((px + py + pz) & 1) != 0) return -1;
+  if (px == 0 && py == 0 && pz == 0) return 0;
+  return px == 0 ? 1 : (py == 0 ? 2 : 3);
+}
+
+__host__ __device__ constexpr int shell_start(int kind, int m) {
+  int s = 0;
+  for (int i = 0; i < m; ++i) s += shell_z(kind, i);
+  return s;
+}
+
+
+// ---------------------------------------------------------------------------
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC11): per round two 32x32
+// multiplications by fixed odd constants; the high halves are xor-ed with
+// the untouched counter words and the round key; the key advances by two Weyl
+// increments between rounds.
+// ---------------------------------------------------------------------------
+struct U4 { uint32_t x, y, z, w; };
+
+__host__ __device__ __forceinline__ uint32_t mulhi32(uint32_t a, uint32_t b) {
+#ifdef __CUDA_ARCH__
+  return __umulhi(a, b);
+#else
+  return static_cast<uint32_t>((static_cast<uint64_t>(a) * b) >> 32);
+#endif
+}
+
+__host__ __device__ __forceinline__ U4 philox4x32_10(uint32_t c0, uint32_t c1, uint32_t c2,
+                                                     uint32_t c3, uint32_t k0, uint32_t k1) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    const uint32_t a_lo = 0xD2511F53u * c0, a_hi = mulhi32(0xD2511F53u, c0);
+    const uint32_t b_lo = 0xCD9E8D57u * c2, b_hi = mulhi32(0xCD9E8D57u, c2);
+    const uint32_t n0 = b_hi ^ c1 ^ k0;
+    const uint32_t n2 = a_hi ^ c3 ^ k1;
+    c0 = n0;
+    c1 = b_lo;
+    c2 = n2;
+    c3 = a_lo;
+    k0 += 0x9E3779B9u;
+    k1 += 0xBB67AE85u;
+  }
+  return U4{c0, c1, c2, c3};
+}
+
+// Metropolis threshold: exp(-beta dE) scaled by 2^32, from three 512-entry
+// tables indexed by the bin index idx = dE >> s (dE > 0, idx < 2^27).
+__host__ __device__ __forceinline__ uint32_t compose_threshold(uint32_t t0, uint32_t t1,
+                                                              uint32_t t2) {
+  return mulhi32(mulhi32(t0, t1), t2);
+}
+
+// ---------------------------------------------------------------------------
+// Launch parameters.
+// ---------------------------------------------------------------------------
+struct Geom {
+  int kind, nb;
+  int n[3];
+  int m[3];       // link cells per dimension (even, or 1)
+  int L;          // nominal cell edge (conventional cells)
+  int K, M;       // species, shells in use
+  int z1;         // first-shell coordination
+  int pack4;      // occupancy stored two sites per byte
+  uint32_t seed_lo, seed_hi;
+};
+
+struct PhaseArgs {
+  uint32_t t;      // global sweep index
+  int shift[3];    // link-cell origin of this sweep
+  int colour;      // 0..7
+  int mode, s;     // acceptance mode, bin shift
+};
+
+struct Tables {
+  uint32_t w[kTabWords];
+};
+
+// Device-side statistics block inside the workspace: [0..3] this call,
+// [4..7] since the running energy was last (re)started, [8] error status.
+constexpr int kStatCall = 0;
+constexpr int kStatCum = 4;
+constexpr int kStatStatus = 8;
+
+// Shell vectors of one lattice kind for device lookups (generic kernels).
+struct ShellParam {
+  int8_t v[kMaxShellVecs][3];
+  int start[kMaxShells + 1];
+};
+
+}  // namespace smcx

@@ -15,8 +15,9 @@ Recipes:
                       or fractions -> largest-remainder rounding, ties to the
                       lower id.
   dirichlet_fractions Dirichlet(alpha,...,alpha) from PCG64(seed).
-  initial_occupancy   species-sorted array of those counts, permuted by
-                      PCG64(seed).shuffle; canonical site order
+  initial_occupancy   those exact counts at random sites (PCG64(seed)
+                      shuffle up to 2^26 sites, i.i.d. draw + random
+                      rebalancing above); canonical site order
                       ((z*ny + y)*nx + x)*nb + b.
 """
 from __future__ import annotations
@@ -74,11 +75,43 @@ def dirichlet_fractions(K: int, alpha: float, seed: int) -> np.ndarray:
 
 
 def initial_occupancy(kind: int, n, K: int, seed: int, fractions=None) -> np.ndarray:
+    """Exact composition counts at random positions.  Up to 2^26 sites: the
+    species-sorted array shuffled by PCG64(seed).  Larger lattices (where a
+    full shuffle takes minutes): species drawn i.i.d. with the target
+    fractions, then the surplus sites of over-represented species, picked at
+    random, are reassigned to under-represented ones until the counts are
+    exact."""
     N = n_sites(kind, n)
     counts = composition_counts(N, K, fractions)
-    occ = np.repeat(np.arange(K, dtype=np.uint8), counts)
     rng = np.random.Generator(np.random.PCG64(seed))
-    rng.shuffle(occ)
+    if N <= (1 << 26):
+        occ = np.repeat(np.arange(K, dtype=np.uint8), counts)
+        rng.shuffle(occ)
+        return occ
+    cum = np.cumsum(counts)
+    occ = np.empty(N, dtype=np.uint8)
+    chunk = 1 << 24
+    for start in range(0, N, chunk):
+        stop = min(N, start + chunk)
+        if fractions is None:
+            occ[start:stop] = rng.integers(0, K, stop - start, dtype=np.uint8)
+        else:
+            u = rng.integers(0, N, stop - start, dtype=np.int64)
+            occ[start:stop] = np.searchsorted(cum, u, side="right").astype(np.uint8)
+    have = np.bincount(occ, minlength=K).astype(np.int64)
+    surplus = {s: int(have[s] - counts[s]) for s in range(K) if have[s] > counts[s]}
+    deficit = [(s, int(counts[s] - have[s])) for s in range(K) if have[s] < counts[s]]
+    pool = []
+    for s, e in surplus.items():
+        idx = np.flatnonzero(occ == s)
+        pool.append(idx[rng.choice(len(idx), size=e, replace=False)])
+    if pool:
+        pool = np.concatenate(pool)
+        rng.shuffle(pool)
+        pos = 0
+        for s, e in deficit:
+            occ[pool[pos:pos + e]] = s
+            pos += e
     return occ
 
 

@@ -1,0 +1,158 @@
+"""Python handle over one lattice of the C ABI (include/smcx.h).
+
+PyTorch provides the device buffers (occupancy, workspace) and the CUDA
+stream; every computation runs inside libsmcx.so.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+
+from . import _lib
+from ._lib import LatticeDesc, SweepStats, check
+
+BCC, FCC = 0, 1
+NO_SHIFT, SINGLE_CELL = 1, 2
+OPT_KERNEL, OPT_TILE = 1, 2
+KERNEL_AUTO, KERNEL_GENERIC, KERNEL_TILED = 0, 1, 2
+
+
+def make_desc(kind, n, n_species, pack_bits=8, min_cell=0, flags=0, seed=0) -> LatticeDesc:
+    d = LatticeDesc()
+    d.kind = int(kind)
+    d.n[0], d.n[1], d.n[2] = (int(v) for v in n)
+    d.n_species = int(n_species)
+    d.pack_bits = int(pack_bits)
+    d.min_cell = int(min_cell)
+    d.flags = int(flags)
+    d.seed = int(seed)
+    return d
+
+
+def _host_ptr(a: np.ndarray):
+    return ctypes.c_void_p(a.ctypes.data)
+
+
+class Lattice:
+    """One simulated lattice.  occ: canonical uint8 occupancy (host array)."""
+
+    def __init__(self, kind, n, n_species, occ, seed=0, pack_bits=8, min_cell=0, flags=0,
+                 device=None, stream=None):
+        import torch
+
+        self._torch = torch
+        self.L = _lib.lib()
+        self.desc = make_desc(kind, n, n_species, pack_bits, min_cell, flags, seed)
+        self.kind, self.n, self.K = int(kind), tuple(int(v) for v in n), int(n_species)
+        self.N = (2 if self.kind == BCC else 4) * self.n[0] * self.n[1] * self.n[2]
+        occ = np.ascontiguousarray(occ, dtype=np.uint8)
+        if occ.size != self.N:
+            raise ValueError(f"occupancy has {occ.size} sites, lattice needs {self.N}")
+        dev = torch.device("cuda", torch.cuda.current_device() if device is None else device)
+        self.device = dev
+        self.stream = stream if stream is not None else torch.cuda.current_stream(dev)
+        ob = self.L.smcx_occupancy_bytes(ctypes.byref(self.desc))
+        wb = self.L.smcx_workspace_bytes(ctypes.byref(self.desc))
+        if ob == 0 or wb == 0:
+            raise _lib.SmcxError(_lib.SMCX_EINVAL, "invalid lattice descriptor")
+        # torch's caching allocator returns 512-byte aligned blocks
+        self.d_occ = torch.empty(ob, dtype=torch.uint8, device=dev)
+        self.d_work = torch.empty(wb, dtype=torch.uint8, device=dev)
+        h = ctypes.c_void_p()
+        with torch.cuda.device(dev):
+            check(self.L.smcx_create_lattice(ctypes.byref(self.desc),
+                                             ctypes.c_void_p(self.d_occ.data_ptr()),
+                                             ctypes.c_void_p(self.d_work.data_ptr()),
+                                             _host_ptr(occ), ctypes.c_void_p(self.stream.cuda_stream),
+                                             ctypes.byref(h)))
+        self.h = h
+        self.M = 0
+
+    # ------------------------------------------------------------------
+    def close(self):
+        if getattr(self, "h", None) is not None and self.h.value:
+            self.L.smcx_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_epi(self, V):
+        V = np.ascontiguousarray(V, dtype=np.int64)
+        if V.ndim != 3 or V.shape[1] != self.K or V.shape[2] != self.K:
+            raise ValueError("EPI table must be [M][K][K]")
+        check(self.L.smcx_set_epi(self.h, V.shape[0], _host_ptr(V)))
+        self.M = V.shape[0]
+
+    def set_option(self, key, value):
+        check(self.L.smcx_set_option(self.h, int(key), int(value)))
+
+    def sweep(self, n_sweeps=1, T_first=1000.0, T_last=None, stats=True):
+        T_last = T_first if T_last is None else T_last
+        st = SweepStats()
+        check(self.L.smcx_sweep(self.h, int(n_sweeps), float(T_first), float(T_last),
+                                ctypes.byref(st) if stats else None))
+        return st.as_dict() if stats else None
+
+    def run_colour(self, colour, T):
+        st = SweepStats()
+        check(self.L.smcx_run_colour(self.h, int(colour), float(T), ctypes.byref(st)))
+        return st.as_dict()
+
+    def energy(self) -> int:
+        e = ctypes.c_int64()
+        check(self.L.smcx_energy(self.h, ctypes.byref(e)))
+        return int(e.value)
+
+    def running_energy(self) -> int:
+        e = ctypes.c_int64()
+        check(self.L.smcx_running_energy(self.h, ctypes.byref(e)))
+        return int(e.value)
+
+    def sro(self, n_shells):
+        cnt = np.zeros((n_shells, self.K, self.K), dtype=np.uint64)
+        alpha = np.zeros((n_shells, self.K, self.K), dtype=np.float64)
+        check(self.L.smcx_warren_cowley_sro(self.h, int(n_shells), _host_ptr(cnt), _host_ptr(alpha)))
+        return cnt, alpha
+
+    def occupancy(self) -> np.ndarray:
+        out = np.empty(self.N, dtype=np.uint8)
+        check(self.L.smcx_get_occupancy(self.h, _host_ptr(out)))
+        return out
+
+    def set_occupancy(self, occ):
+        occ = np.ascontiguousarray(occ, dtype=np.uint8)
+        if occ.size != self.N:
+            raise ValueError("wrong occupancy size")
+        check(self.L.smcx_set_occupancy(self.h, _host_ptr(occ)))
+
+    @property
+    def sweep_counter(self) -> int:
+        t = ctypes.c_uint32()
+        check(self.L.smcx_get_sweep_counter(self.h, ctypes.byref(t)))
+        return int(t.value)
+
+    @sweep_counter.setter
+    def sweep_counter(self, t):
+        check(self.L.smcx_set_sweep_counter(self.h, int(t)))
+
+    def layout(self):
+        L = ctypes.c_uint32()
+        m = (ctypes.c_uint32 * 3)()
+        check(self.L.smcx_get_layout(self.h, ctypes.byref(L), m))
+        return int(L.value), tuple(int(v) for v in m)
+
+    def checkpoint(self) -> bytes:
+        n = ctypes.c_size_t()
+        check(self.L.smcx_checkpoint(self.h, None, ctypes.byref(n)))
+        buf = ctypes.create_string_buffer(n.value)
+        check(self.L.smcx_checkpoint(self.h, buf, ctypes.byref(n)))
+        return buf.raw[: n.value]
+
+    def restore(self, blob: bytes):
+        buf = ctypes.create_string_buffer(blob, len(blob))
+        check(self.L.smcx_restore(self.h, buf, len(blob)))
