@@ -1,0 +1,342 @@
+#!/usr/bin/env python3
+"""Benchmark of the SMC-X swap sweep on GB300 (one JSON line on rank 0).
+
+Workload (default): BCC 812^3 conventional cells x 2 = 1,070,774,656 sites,
+5 species equiatomic, EPI shells 1-3 drawn from N(0, 0.02 eV) (seed 0,
+quantised to 2^-32 eV), linear anneal 1200 -> 600 K over 10^4 sweeps, Philox
+seed 0, one byte per site.  One step = one MC sweep (the eight checkerboard
+colour phases, one trial per site) at that sweep's anneal temperature plus
+one Warren-Cowley SRO / energy pair-count reduction, with the pair counts
+read back to the host.  Inputs (1.07 GB of occupancy) exceed the 129 MB L2,
+so no flush is needed between steps.
+
+Metric: attempted swaps per second (sites x sweeps / device time of the
+timed steps, max over ranks).  Multi-GPU: one independent lattice replica
+per rank (the sweep of one lattice has no exchange step), value = sum.
+
+--impl reference times the sequential CPU oracle (oracle/) on a bounded
+sample of the same workload on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+from paper_2509_20949_gb300 import inputs  # noqa: E402
+
+METRIC = "attempted MC swaps/sec on 1 GB300 (plain single-lattice sweep)"
+UNIT = "swaps/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="bcc812_k5")
+    ap.add_argument("--kernel", type=int, default=0, help="0 auto, 1 generic, 2 tiled")
+    ap.add_argument("--pack-bits", type=int, default=8)
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    return ap.parse_args()
+
+
+def workload_config(name):
+    w = inputs.workload(name)
+    kind = "BCC" if w["kind"] == 0 else "FCC"
+    n = w["n"]
+    N = inputs.n_sites(w["kind"], n)
+    desc = (f"{name}: {kind} {n[0]}x{n[1]}x{n[2]} conventional cells = {N} sites, K={w['K']}, "
+            f"EPI shells 1-{w['M']} ~N(0,{w['sigma']} eV) seed {w['epi_seed']}, "
+            f"T {w['T_first']:g}->{w['T_last']:g} K over {w['sweeps']} sweeps, Philox seed {w['seed']}")
+    return w, N, desc
+
+
+def sweep_temperature(w, i):
+    n = w["sweeps"]
+    if n <= 1 or w["T_first"] == w["T_last"]:
+        return w["T_first"]
+    return w["T_first"] + (w["T_last"] - w["T_first"]) * (i % n) / (n - 1)
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle sampling during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{gpu_index}.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    smax.append(float(parts[2]))
+                except ValueError:
+                    continue
+                for nm, v in zip(names, parts[5:9]):
+                    if v.lower().startswith("active"):
+                        reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def cpu_baseline(w, N, V, occ, seconds, rank):
+    """The oracle as it stands, single-threaded on the host, replaying the
+    trials of a bounded sample of link cells of colour 0 of sweep 0 on the
+    full lattice."""
+    import oracle
+
+    d = oracle.Desc(w["kind"], w["n"], w["K"], w["M"], seed=w["seed"])
+    cids = _colour_cells(oracle, d, 0)
+    scratch = np.array(occ, copy=True)
+    T = sweep_temperature(w, 0)
+    # calibrate on a small sample, then run ~`seconds` of work
+    n_cal = 256
+    t0 = time.perf_counter()
+    _, st = oracle.phase_cells(d, V, scratch, 0, T, 0, cids[:n_cal], inplace=True)
+    dt = time.perf_counter() - t0
+    per_cell = max(dt / n_cal, 1e-7)
+    n = int(min(len(cids) - n_cal, max(64, seconds / per_cell)))
+    t0 = time.perf_counter()
+    _, st = oracle.phase_cells(d, V, scratch, 0, T, 0, cids[n_cal:n_cal + n], inplace=True)
+    dt = time.perf_counter() - t0
+    att = int(st["attempts"])
+    return {"value": att / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{n} link cells ({att} trials) of colour 0, sweep 0 of the full lattice, "
+                      f"{dt:.1f} s single-threaded"}
+
+
+def _colour_cells(oracle, d, colour):
+    L, m = oracle.layout(d)
+    cx = np.arange(m[0])
+    cy = np.arange(m[1])
+    cz = np.arange(m[2])
+    Z, Y, X = np.meshgrid(cz, cy, cx, indexing="ij")
+    col = (X & 1) | ((Y & 1) << 1) | ((Z & 1) << 2)
+    cid = (Z * m[1] + Y) * m[0] + X
+    return cid[col == colour].astype(np.uint32).ravel()
+
+
+def run_reference(args):
+    world, rank, local = dist_setup()
+    if world > 1 and rank != 0:
+        return 0
+    w, N, desc = workload_config(args.workload)
+    V = inputs.epi_table(w["M"], w["K"], w["sigma"], w["epi_seed"])
+    occ = inputs.initial_occupancy(w["kind"], w["n"], w["K"], w["occ_seed"], w["fractions"])
+    import oracle
+
+    oracle.build()
+    d = oracle.Desc(w["kind"], w["n"], w["K"], w["M"], seed=w["seed"])
+    cids = _colour_cells(oracle, d, 0)
+    per_step = max(64, min(32768, len(cids) // max(1, args.steps + args.warmup)))
+    scratch = np.array(occ, copy=True)
+    pos = 0
+    times, atts = [], []
+    for s in range(args.warmup + args.steps):
+        sel = cids[pos:pos + per_step]
+        pos += per_step
+        t0 = time.perf_counter()
+        _, st = oracle.phase_cells(d, V, scratch, 0, sweep_temperature(w, 0), 0, sel, inplace=True)
+        dt = time.perf_counter() - t0
+        if s >= args.warmup:
+            times.append(dt)
+            atts.append(int(st["attempts"]))
+    value = sum(atts) / sum(times)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * sum(times) / len(times), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+            "config": {"workload": desc, "sample_per_step": f"{per_step} link cells of colour 0"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"{per_step} link cells per step of colour 0, sweep 0, "
+                                       "full lattice in host memory"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    import torch
+
+    world, rank, local = dist_setup()
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    from paper_2509_20949_gb300.lattice import Lattice
+
+    w, N, desc = workload_config(args.workload)
+    V = inputs.epi_table(w["M"], w["K"], w["sigma"], w["epi_seed"])
+    occ = inputs.initial_occupancy(w["kind"], w["n"], w["K"], w["occ_seed"], w["fractions"])
+    seed = w["seed"] + rank  # independent replica per rank
+    stream = torch.cuda.current_stream()
+    lat = Lattice(w["kind"], w["n"], w["K"], occ, seed=seed, pack_bits=args.pack_bits,
+                  stream=stream)
+    if args.kernel:
+        lat.set_option(1, args.kernel)
+    lat.set_epi(V)
+    M = w["M"]
+
+    def step(i):
+        lat.sweep(1, sweep_temperature(w, i), stats=False)
+
+    # warm-up
+    for i in range(args.warmup):
+        step(i)
+        lat.sro(M)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    ev_sweep = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                for _ in range(args.steps)]
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for s in range(args.steps):
+        a, b = ev_sweep[s]
+        a.record(stream)
+        step(args.warmup + s)
+        b.record(stream)
+        lat.sro(M)  # pair counts -> host (the step's result)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    t_ms = ev0.elapsed_time(ev1)
+    sweep_ms = sum(a.elapsed_time(b) for a, b in ev_sweep)
+    if world > 1:
+        tt = torch.tensor([t_ms], device="cuda")
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        t_ms = float(tt.item())
+    total_attempts = N * args.steps * world
+    value = total_attempts / (t_ms / 1e3)
+    launches_per_sweep = 8
+    kernel_ms = sweep_ms / (args.steps * launches_per_sweep)
+    alg_bytes_per_launch = 2.0 * N / launches_per_sweep * (0.5 if args.pack_bits == 4 else 1.0)
+    peak, peak_src = measured_peaks()
+    achieved = alg_bytes_per_launch / (kernel_ms / 1e3) / 1e9
+
+    # end to end through the public API with host buffers
+    h_in = torch.empty(N, dtype=torch.uint8, pin_memory=True)
+    h_in.numpy()[:] = lat.occupancy()
+    h_out = torch.empty(N, dtype=torch.uint8, pin_memory=True)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for s in range(args.e2e_steps):
+        lat.set_occupancy(h_in.numpy())
+        step(args.warmup + args.steps + s)
+        cnt, _ = lat.sro(M)
+        h_out.numpy()[:] = lat.occupancy()
+        h_in, h_out = h_out, h_in
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    e2e_value = N * args.e2e_steps / e2e_s
+    if world > 1:
+        tt = torch.tensor([e2e_s], device="cuda")
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        e2e_value = N * args.e2e_steps * world / float(tt.item())
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(w, N, V, occ, args.cpu_seconds, rank)
+    traffic = _recorded_traffic()
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": t_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+            "config": {"workload": desc, "step": "1 sweep (8 colour phases) + 1 SRO/energy pair count",
+                       "l2": "no flush: 1.07 GB occupancy > 129 MB L2",
+                       "pack_bits": args.pack_bits, "parallelism": f"replicas x{world}"},
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": N,
+                    "d2h_bytes_per_step": N + 8 * M * w["K"] * w["K"]},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": traffic,
+                         "kernel": "sweep phase", "kernel_ms_per_launch": kernel_ms,
+                         "peak_source": peak_src},
+            "cpu_baseline": cpu,
+            "clocks": clk,
+            "gpu_launches": args.steps * (launches_per_sweep + 1),
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def _recorded_traffic():
+    return None
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -183,6 +183,12 @@ smcx_status smcx_set_option(smcx_lattice* lat, uint32_t key, int64_t value);
 uint32_t smcx_tile_shape_count(uint32_t kind);
 smcx_status smcx_tile_shape(uint32_t kind, uint32_t i, uint32_t* cells_xyz);
 
+/* Kernel the next sweep will use for this lattice and EPI: *kernel = 1
+   (generic, global memory) or 2 (tiled, shared-memory tiles + halos) and
+   *tile_shape = the tile shape index (-1 for the generic kernel).
+   ESTATE: no EPI. */
+smcx_status smcx_kernel_in_use(smcx_lattice* lat, uint32_t* kernel, int32_t* tile_shape);
+
 /* Releases the handle (never the caller's buffers). */
 smcx_status smcx_destroy(smcx_lattice* lat);
 

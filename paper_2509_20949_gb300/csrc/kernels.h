@@ -10,10 +10,45 @@ cudaError_t launch_sweep_generic(const Geom& g, const PhaseArgs& a, const ShellP
                                  unsigned long long* stats, cudaStream_t st);
 
 cudaError_t launch_pair_count_generic(const Geom& g, const ShellParam& sp, int n_shells,
-                                      const uint8_t* occ, unsigned long long* counts, uint32_t N,
-                                      int n_sm, cudaStream_t st);
+                                      const uint8_t* occ, unsigned long long* counts,
+                                      uint32_t n_cells, int n_sm, cudaStream_t st);
+
+cudaError_t launch_canon_to_dev(const Geom& g, const uint8_t* canon, uint8_t* occ,
+                                uint32_t n_cells, int n_sm, cudaStream_t st);
+cudaError_t launch_dev_to_canon(const Geom& g, const uint8_t* occ, uint8_t* canon,
+                                uint32_t n_cells, int n_sm, cudaStream_t st);
+cudaError_t launch_validate(const uint8_t* canon, uint64_t n, uint32_t K, unsigned int* flag,
+                            int n_sm, cudaStream_t st);
 
 cudaError_t launch_philox_fill(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3, uint64_t key,
                                uint32_t n, uint32_t* out, cudaStream_t st);
 
+// ---- tiled sweep (shared-memory tiles + halos) ---------------------------
+// Per-(p, q) rows of the energy-difference table used by the tiled kernel.
+struct TiledEpi {
+  int kmax;        // 5 or 6 (species classes compiled)
+  int row_words;   // 32-bit words per (code_p, code_q) row
+  int n_rows;      // rows in the table
+  const uint32_t* d_table;
+};
+
+// Returns cudaErrorNotSupported (without launching) when no compiled tile
+// shape fits the lattice; the caller then uses the generic kernel.
+cudaError_t launch_sweep_tiled(const Geom& g, const PhaseArgs& a, const Tables& tab, uint8_t* occ,
+                               const TiledEpi& epi, unsigned long long* stats, int shape,
+                               cudaStream_t st);
+bool tiled_supported(const Geom& g, int shape);
+int tiled_shape_count(int kind);
+void tiled_shape_cells(int kind, int shape, int cells[3]);
+
+// table layout helpers shared by the host table builder and the kernel
+int tiled_row_words(int M, int kmax);
+
+}  // namespace smcx
+
+namespace smcx {
+// tiled half-shell pair counts (see pair_tiled.cu); rows of K_MAX = K <= 5 ? 5 : 6
+cudaError_t launch_pair_count_tiled(const Geom& g, int n_shells, const uint8_t* occ,
+                                    unsigned long long* h, int n_sm, cudaStream_t st,
+                                    bool check_only);
 }  // namespace smcx

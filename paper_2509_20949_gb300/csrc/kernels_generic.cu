@@ -1,8 +1,10 @@
 // kernels_generic.cu -- global-memory sweep and pair-count kernels for any
 // lattice size (including lattices so small that a site is its own
-// neighbour).  One thread runs all trials of one link cell of the active
-// colour (Sec. 2.2: cells of one colour never interact); every neighbour
-// index is computed from coordinates with periodic wrap.
+// neighbour), plus the conversions between the canonical occupancy and the
+// device storage.  In the sweep, one thread runs all trials of one link cell
+// of the active colour (Sec. 2.2: cells of one colour never interact);
+// every neighbour is located from coordinates with periodic wrap.
+#include "device_util.cuh"
 #include "kernels.h"
 
 namespace smcx {
@@ -12,68 +14,41 @@ __device__ __forceinline__ int pmod(int a, int n) {
   return r < 0 ? r + n : r;
 }
 
-__device__ __forceinline__ uint32_t occ_get(const uint8_t* occ, uint32_t i, int pack4) {
-  if (!pack4) return occ[i];
-  return (occ[i >> 1] >> ((i & 1u) * 4u)) & 15u;
-}
-
-__device__ __forceinline__ void occ_set(uint8_t* occ, uint32_t i, uint32_t v, int pack4) {
-  if (!pack4) {
-    occ[i] = static_cast<uint8_t>(v);
-    return;
-  }
-  uint8_t* p = occ + (i >> 1);
-  const uint32_t sh = (i & 1u) * 4u;
-  *p = static_cast<uint8_t>((*p & ~(15u << sh)) | (v << sh));
-}
-
 struct SiteXYZ {
   int x, y, z, b;
 };
 
-__device__ __forceinline__ uint32_t site_of(const Geom& g, int x, int y, int z, int b) {
-  return ((static_cast<uint32_t>(z) * g.n[1] + y) * g.n[0] + x) * g.nb + b;
+__device__ __forceinline__ uint32_t occ_get(const Geom& g, const uint8_t* occ, const SiteXYZ& s) {
+  if (!g.pack4) return static_cast<uint32_t>(occ[dev_row(g, s.b, s.z, s.y) + s.x]) / g.W;
+  return (occ[dev_row(g, s.b >> 1, s.z, s.y) + s.x] >> ((s.b & 1) * 4)) & 15u;
 }
 
-__device__ __forceinline__ SiteXYZ xyz_of(const Geom& g, uint32_t i) {
-  SiteXYZ s;
-  s.b = static_cast<int>(i % g.nb);
-  uint32_t c = i / g.nb;
-  s.x = static_cast<int>(c % g.n[0]);
-  c /= g.n[0];
-  s.y = static_cast<int>(c % g.n[1]);
-  s.z = static_cast<int>(c / g.n[1]);
-  return s;
+__device__ __forceinline__ void occ_set(const Geom& g, uint8_t* occ, const SiteXYZ& s, uint32_t v) {
+  if (!g.pack4) {
+    occ[dev_row(g, s.b, s.z, s.y) + s.x] = static_cast<uint8_t>(v * g.W);
+    return;
+  }
+  uint8_t* p = occ + dev_row(g, s.b >> 1, s.z, s.y) + s.x;
+  const uint32_t sh = (s.b & 1) * 4u;
+  *p = static_cast<uint8_t>((*p & ~(15u << sh)) | (v << sh));
 }
 
-__device__ __forceinline__ uint32_t neighbour(const Geom& g, const SiteXYZ& s, int dx, int dy,
-                                              int dz) {
+// canonical site index ((z*ny + y)*nx + x)*nb + b: the identity of a site
+__device__ __forceinline__ uint32_t site_id(const Geom& g, const SiteXYZ& s) {
+  return ((static_cast<uint32_t>(s.z) * g.n[1] + s.y) * g.n[0] + s.x) * g.nb + s.b;
+}
+
+__device__ __forceinline__ SiteXYZ neighbour(const Geom& g, const SiteXYZ& s, int dx, int dy,
+                                             int dz) {
   const int hx = pmod(2 * s.x + basis_comp(g.kind, s.b, 0) + dx, 2 * g.n[0]);
   const int hy = pmod(2 * s.y + basis_comp(g.kind, s.b, 1) + dy, 2 * g.n[1]);
   const int hz = pmod(2 * s.z + basis_comp(g.kind, s.b, 2) + dz, 2 * g.n[2]);
-  const int bp = basis_of_parity(g.kind, hx & 1, hy & 1, hz & 1);
-  return site_of(g, hx >> 1, hy >> 1, hz >> 1, bp);
-}
-
-__device__ __forceinline__ void warp_reduce_add_stats(unsigned long long* stats, uint64_t att,
-                                                      uint64_t unl, uint64_t acc, int64_t de) {
-#pragma unroll
-  for (int off = 16; off > 0; off >>= 1) {
-    att += __shfl_down_sync(0xffffffffu, att, off);
-    unl += __shfl_down_sync(0xffffffffu, unl, off);
-    acc += __shfl_down_sync(0xffffffffu, acc, off);
-    de += __shfl_down_sync(0xffffffffu, de, off);
-  }
-  if ((threadIdx.x & 31) == 0) {
-    atomicAdd(stats + kStatCall + 0, att);
-    atomicAdd(stats + kStatCall + 1, unl);
-    atomicAdd(stats + kStatCall + 2, acc);
-    atomicAdd(stats + kStatCall + 3, static_cast<unsigned long long>(de));
-    atomicAdd(stats + kStatCum + 0, att);
-    atomicAdd(stats + kStatCum + 1, unl);
-    atomicAdd(stats + kStatCum + 2, acc);
-    atomicAdd(stats + kStatCum + 3, static_cast<unsigned long long>(de));
-  }
+  SiteXYZ r;
+  r.x = hx >> 1;
+  r.y = hy >> 1;
+  r.z = hz >> 1;
+  r.b = basis_of_parity(g.kind, hx & 1, hy & 1, hz & 1);
+  return r;
 }
 
 // One colour phase.  Thread -> active cell (cx, cy, cz) with c_d = 2 a_d + bit_d
@@ -120,14 +95,14 @@ __global__ void __launch_bounds__(128) k_sweep_generic(const Geom g, const Phase
             si.y = pmod(ys + a.shift[1], g.n[1]);
             si.z = pmod(zs + a.shift[2], g.n[2]);
             si.b = b;
-            const uint32_t i = site_of(g, si.x, si.y, si.z, b);
+            const uint32_t i = site_id(g, si);
             if ((k & 1u) == 0) w = philox4x32_10(k >> 1, cid, a.t, 0u, g.seed_lo, g.seed_hi);
             const uint32_t wa = (k & 1u) ? w.z : w.x;
             const uint32_t wb = (k & 1u) ? w.w : w.y;
             const uint32_t dir = mulhi32(wa, static_cast<uint32_t>(g.z1));
-            const uint32_t j = neighbour(g, si, sp.v[dir][0], sp.v[dir][1], sp.v[dir][2]);
-            const SiteXYZ sj = xyz_of(g, j);
-            const uint32_t p = occ_get(occ, i, g.pack4), q = occ_get(occ, j, g.pack4);
+            const SiteXYZ sj = neighbour(g, si, sp.v[dir][0], sp.v[dir][1], sp.v[dir][2]);
+            const uint32_t j = site_id(g, sj);
+            const uint32_t p = occ_get(g, occ, si), q = occ_get(g, occ, sj);
             ++att;
             if (p == q) continue;
             ++unl;
@@ -135,14 +110,16 @@ __global__ void __launch_bounds__(128) k_sweep_generic(const Geom g, const Phase
             for (int m = 0; m < g.M; ++m) {
               const int64_t* Vm = V + static_cast<int64_t>(m) * K * K;
               for (int t = sp.start[m]; t < sp.start[m + 1]; ++t) {
-                const uint32_t ki = neighbour(g, si, sp.v[t][0], sp.v[t][1], sp.v[t][2]);
-                if (ki != i && ki != j) {
-                  const uint32_t sk = occ_get(occ, ki, g.pack4);
+                const SiteXYZ ki = neighbour(g, si, sp.v[t][0], sp.v[t][1], sp.v[t][2]);
+                const uint32_t ik = site_id(g, ki);
+                if (ik != i && ik != j) {
+                  const uint32_t sk = occ_get(g, occ, ki);
                   de += Vm[q * K + sk] - Vm[p * K + sk];
                 }
-                const uint32_t kj = neighbour(g, sj, sp.v[t][0], sp.v[t][1], sp.v[t][2]);
-                if (kj != i && kj != j) {
-                  const uint32_t sk = occ_get(occ, kj, g.pack4);
+                const SiteXYZ kj = neighbour(g, sj, sp.v[t][0], sp.v[t][1], sp.v[t][2]);
+                const uint32_t jk = site_id(g, kj);
+                if (jk != i && jk != j) {
+                  const uint32_t sk = occ_get(g, occ, kj);
                   de += Vm[p * K + sk] - Vm[q * K + sk];
                 }
               }
@@ -159,14 +136,14 @@ __global__ void __launch_bounds__(128) k_sweep_generic(const Geom g, const Phase
               if (idx >= (1ull << 27)) {
                 accept = false;
               } else {
-                const uint32_t thr = compose_threshold(s_tab[idx & 511u], s_tab[512 + ((idx >> 9) & 511u)],
-                                                       s_tab[1024 + (idx >> 18)]);
+                const uint32_t thr = compose_threshold(
+                    s_tab[idx & 511u], s_tab[512 + ((idx >> 9) & 511u)], s_tab[1024 + (idx >> 18)]);
                 accept = wb < thr;
               }
             }
             if (accept) {
-              occ_set(occ, i, q, g.pack4);
-              occ_set(occ, j, p, g.pack4);
+              occ_set(g, occ, si, q);
+              occ_set(g, occ, sj, p);
               ++acc;
               sum_de += de;
             }
@@ -181,7 +158,7 @@ __global__ void __launch_bounds__(256) k_pair_count_generic(const Geom g, const 
                                                            int n_shells,
                                                            const uint8_t* __restrict__ occ,
                                                            unsigned long long* __restrict__ counts,
-                                                           uint32_t N) {
+                                                           uint32_t n_cells) {
   extern __shared__ uint32_t s_cnt[];
   const int K = g.K;
   const bool in_smem = K <= 32;
@@ -189,24 +166,86 @@ __global__ void __launch_bounds__(256) k_pair_count_generic(const Geom g, const 
   if (in_smem)
     for (int c = threadIdx.x; c < n_cnt; c += blockDim.x) s_cnt[c] = 0;
   __syncthreads();
-  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
-    const SiteXYZ s = xyz_of(g, i);
-    const uint32_t pc = occ_get(occ, i, g.pack4);
-    for (int m = 0; m < n_shells; ++m)
-      for (int t = sp.start[m]; t < sp.start[m + 1]; ++t) {
-        const uint32_t k = neighbour(g, s, sp.v[t][0], sp.v[t][1], sp.v[t][2]);
-        const uint32_t p = occ_get(occ, k, g.pack4);
-        const int slot = (m * K + pc) * K + p;
-        if (in_smem)
-          atomicAdd(&s_cnt[slot], 1u);
-        else
-          atomicAdd(&counts[slot], 1ull);
-      }
+  for (uint32_t cell = blockIdx.x * blockDim.x + threadIdx.x; cell < n_cells;
+       cell += gridDim.x * blockDim.x) {
+    SiteXYZ s;
+    s.x = static_cast<int>(cell % g.n[0]);
+    s.y = static_cast<int>((cell / g.n[0]) % g.n[1]);
+    s.z = static_cast<int>(cell / (static_cast<uint32_t>(g.n[0]) * g.n[1]));
+    for (int b = 0; b < g.nb; ++b) {
+      s.b = b;
+      const uint32_t pc = occ_get(g, occ, s);
+      for (int m = 0; m < n_shells; ++m)
+        for (int t = sp.start[m]; t < sp.start[m + 1]; ++t) {
+          const SiteXYZ k = neighbour(g, s, sp.v[t][0], sp.v[t][1], sp.v[t][2]);
+          const uint32_t p = occ_get(g, occ, k);
+          const int slot = (m * K + pc) * K + p;
+          if (in_smem)
+            atomicAdd(&s_cnt[slot], 1u);
+          else
+            atomicAdd(&counts[slot], 1ull);
+        }
+    }
   }
   __syncthreads();
   if (in_smem)
     for (int c = threadIdx.x; c < n_cnt; c += blockDim.x)
       if (s_cnt[c]) atomicAdd(&counts[c], static_cast<unsigned long long>(s_cnt[c]));
+}
+
+// canonical bytes -> device storage; one thread per conventional cell
+__global__ void k_canon_to_dev(const Geom g, const uint8_t* __restrict__ canon,
+                               uint8_t* __restrict__ occ, uint32_t n_cells) {
+  for (uint32_t cell = blockIdx.x * blockDim.x + threadIdx.x; cell < n_cells;
+       cell += gridDim.x * blockDim.x) {
+    const int x = static_cast<int>(cell % g.n[0]);
+    const int y = static_cast<int>((cell / g.n[0]) % g.n[1]);
+    const int z = static_cast<int>(cell / (static_cast<uint32_t>(g.n[0]) * g.n[1]));
+    const uint8_t* src = canon + static_cast<size_t>(cell) * g.nb;
+    if (!g.pack4) {
+      for (int b = 0; b < g.nb; ++b) occ[dev_row(g, b, z, y) + x] = static_cast<uint8_t>(src[b] * g.W);
+    } else {
+      for (int b = 0; b < g.nb; b += 2)
+        occ[dev_row(g, b >> 1, z, y) + x] = static_cast<uint8_t>(src[b] | (src[b + 1] << 4));
+    }
+  }
+}
+
+__global__ void k_dev_to_canon(const Geom g, const uint8_t* __restrict__ occ,
+                               uint8_t* __restrict__ canon, uint32_t n_cells) {
+  for (uint32_t cell = blockIdx.x * blockDim.x + threadIdx.x; cell < n_cells;
+       cell += gridDim.x * blockDim.x) {
+    const int x = static_cast<int>(cell % g.n[0]);
+    const int y = static_cast<int>((cell / g.n[0]) % g.n[1]);
+    const int z = static_cast<int>(cell / (static_cast<uint32_t>(g.n[0]) * g.n[1]));
+    uint8_t* dst = canon + static_cast<size_t>(cell) * g.nb;
+    if (!g.pack4) {
+      for (int b = 0; b < g.nb; ++b) dst[b] = static_cast<uint8_t>(occ[dev_row(g, b, z, y) + x] / g.W);
+    } else {
+      for (int b = 0; b < g.nb; b += 2) {
+        const uint8_t v = occ[dev_row(g, b >> 1, z, y) + x];
+        dst[b] = v & 15;
+        dst[b + 1] = v >> 4;
+      }
+    }
+  }
+}
+
+// flags[0] |= 1 when a canonical byte is >= K
+__global__ void k_validate(const uint8_t* __restrict__ canon, uint64_t n, uint32_t K,
+                           unsigned int* __restrict__ flag) {
+  bool bad = false;
+  for (uint64_t i = blockIdx.x * static_cast<uint64_t>(blockDim.x) + threadIdx.x; i < n;
+       i += static_cast<uint64_t>(gridDim.x) * blockDim.x)
+    bad |= canon[i] >= K;
+  if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(flag, 1u);
+}
+
+static uint32_t grid_for(uint64_t work, int threads, int n_sm) {
+  uint64_t b = (work + threads - 1) / threads;
+  const uint64_t cap = static_cast<uint64_t>(n_sm > 0 ? n_sm : 148) * 16;
+  if (b > cap) b = cap;
+  return static_cast<uint32_t>(b < 1 ? 1 : b);
 }
 
 cudaError_t launch_sweep_generic(const Geom& g, const PhaseArgs& a, const ShellParam& sp,
@@ -229,15 +268,30 @@ cudaError_t launch_sweep_generic(const Geom& g, const PhaseArgs& a, const ShellP
 }
 
 cudaError_t launch_pair_count_generic(const Geom& g, const ShellParam& sp, int n_shells,
-                                      const uint8_t* occ, unsigned long long* counts, uint32_t N,
-                                      int n_sm, cudaStream_t st) {
+                                      const uint8_t* occ, unsigned long long* counts,
+                                      uint32_t n_cells, int n_sm, cudaStream_t st) {
   const int K = g.K;
   const size_t smem = K <= 32 ? sizeof(uint32_t) * n_shells * K * K : 0;
-  uint32_t blocks = (N + 255) / 256;
-  const uint32_t cap = static_cast<uint32_t>(n_sm) * 8u;
-  if (blocks > cap) blocks = cap;
-  if (blocks == 0) blocks = 1;
-  k_pair_count_generic<<<blocks, 256, smem, st>>>(g, sp, n_shells, occ, counts, N);
+  k_pair_count_generic<<<grid_for(n_cells, 256, n_sm), 256, smem, st>>>(g, sp, n_shells, occ,
+                                                                         counts, n_cells);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_canon_to_dev(const Geom& g, const uint8_t* canon, uint8_t* occ,
+                                uint32_t n_cells, int n_sm, cudaStream_t st) {
+  k_canon_to_dev<<<grid_for(n_cells, 256, n_sm), 256, 0, st>>>(g, canon, occ, n_cells);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_dev_to_canon(const Geom& g, const uint8_t* occ, uint8_t* canon,
+                                uint32_t n_cells, int n_sm, cudaStream_t st) {
+  k_dev_to_canon<<<grid_for(n_cells, 256, n_sm), 256, 0, st>>>(g, occ, canon, n_cells);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_validate(const uint8_t* canon, uint64_t n, uint32_t K, unsigned int* flag,
+                            int n_sm, cudaStream_t st) {
+  k_validate<<<grid_for(n, 256, n_sm), 256, 0, st>>>(canon, n, K, flag);
   return cudaGetLastError();
 }
 

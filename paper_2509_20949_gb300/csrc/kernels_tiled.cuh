@@ -1,0 +1,446 @@
+// kernels_tiled.cuh -- the shared-memory tiled sweep phase.
+//
+// One colour phase of the checkerboard (Sec. 2.2): every active link cell
+// runs its trials sequentially (raster order), cells of one colour run
+// concurrently because they never touch one another's interaction zones.
+// A block owns BX x BY x BZ active cells of the phase; it stages their
+// cells plus a two-conventional-cell halo (the local interaction zone of
+// every trial, Sec. 2.2) from HBM into shared memory with 8-byte vector
+// loads, runs the trials on the shared tile and stores every accepted swap
+// straight back to HBM.
+//
+// Energy change of a trial (EPI model, Sec. 3): with p = sigma_i, q = sigma_j,
+//   dE = sum_m sum_s dx_{m,s} (V_m(q,s) - V_m(p,s)) - (V_1(p,p)+V_1(q,q)-2V_1(p,q)),
+// where dx_{m,s} = (# shell-m neighbours of i of species s) - (same for j):
+// the neighbour species are counted with one-hot SWAR adds (each shared
+// memory byte holds sigma*W, the bit position of species sigma in a W-bit
+// field), the i-j bond, counted once from each side, is removed by the last
+// term.  Because sum_s dx_{m,s} = 0 the s = 0 column folds into the others,
+// and for K <= 5 the two count words are subtracted field-wise with a bias of
+// 32 per field; the constants that leaves are precomputed per (p, q).
+//
+// Shared tile layout: rows (z, y) of pitch RS holding NB sub-rows (one per
+// basis site b) of pitch XW; byte x of sub-row b is site (x, y, z, b).  RS is
+// congruent to 16 modulo 32 bytes so that the 32 lanes of a warp (16 cells
+// along x, 2 along y, cells 2L conventional cells apart) hit 32 distinct
+// banks for every neighbour load.  Shared offsets of every neighbour are
+// compile-time constants (the anchor's basis is unrolled); the partner's
+// basis is fixed for BCC and taken from four class bases for FCC.
+#pragma once
+
+#include <utility>
+
+#include "device_util.cuh"
+#include "kernels.h"
+
+namespace smcx {
+namespace tiled {
+
+__host__ __device__ constexpr int floordiv2(int v) { return v >= 0 ? v / 2 : -((1 - v) / 2); }
+__host__ __device__ constexpr int round_up(int v, int a) { return (v + a - 1) / a * a; }
+
+// parity mask (bit c = component c odd) of basis site b
+__host__ __device__ constexpr int basis_mask(int kind, int b) {
+  return basis_comp(kind, b, 0) | (basis_comp(kind, b, 1) << 1) | (basis_comp(kind, b, 2) << 2);
+}
+__host__ __device__ constexpr int basis_from_mask(int kind, int mask) {
+  return basis_of_parity(kind, mask & 1, (mask >> 1) & 1, (mask >> 2) & 1);
+}
+
+__host__ __device__ constexpr int shell_reach_c(int kind, int M) {
+  int r = 0;
+  for (int i = 0; i < shell_start(kind, M); ++i) {
+    const ShellVec v = shell_vec(kind, i);
+    const int ax = v.x < 0 ? -v.x : v.x, ay = v.y < 0 ? -v.y : v.y, az = v.z < 0 ? -v.z : v.z;
+    r = ax > r ? ax : r;
+    r = ay > r ? ay : r;
+    r = az > r ? az : r;
+  }
+  return r;
+}
+
+template <int KIND_, int M_, int KMAX_, bool PACK4_, int BX_, int BY_, int BZ_>
+struct Cfg {
+  static constexpr int KIND = KIND_, M = M_, KMAX = KMAX_, BX = BX_, BY = BY_, BZ = BZ_;
+  static constexpr bool PACK4 = PACK4_;
+  static constexpr int NB = KIND == 0 ? 2 : 4;
+  static constexpr int HR = shell_reach_c(KIND, M);
+  static constexpr int L = (1 + HR) / 2 + 1;   // link-cell edge (conventional cells)
+  static constexpr int H = 2;                  // halo: reads reach 1 + h_R <= 4 half units
+  static constexpr int SLACK = 2 * L - 1;      // cells of edge L+1 in a ragged dimension
+  static constexpr int EXT_X = (2 * BX - 1) * L + SLACK + 2 * H;
+  static constexpr int EXT_Y = (2 * BY - 1) * L + SLACK + 2 * H;
+  static constexpr int EXT_Z = (2 * BZ - 1) * L + SLACK + 2 * H;
+  static constexpr int XW = round_up(EXT_X + 14, 8);  // 8-byte copy alignment slack
+  static constexpr int RS0 = NB * XW;
+  static constexpr int BANK = BX >= 16 ? 16 : BX;     // lane spacing of the y lanes in banks
+  static constexpr int RS = RS0 + (((BANK - RS0 % 32) % 32) + 32) % 32;
+  static constexpr int PS = RS * EXT_Y;
+  static constexpr int W = KMAX <= 5 ? 6 : 5;
+  static constexpr int NT = BX * BY * BZ;
+  static constexpr int Z1 = shell_z(KIND, 0);
+  static constexpr int NV = shell_start(KIND, M);
+  static constexpr int ROWW = round_up(M * (KMAX - 1) + 2, 2);  // D' words + C (int64)
+  static constexpr int CODES = KMAX * W;                          // rows indexed by codes
+  static constexpr int DROWS = CODES * KMAX;                      // code_p*KMAX + code_q
+  static constexpr int G = PACK4 ? NB / 2 : NB;                   // device row groups
+  static constexpr int TILE_OFF =
+      round_up(4 * (kTabWords + DROWS * ROWW + NB * Z1), 16);     // shared bytes before the tile
+  static_assert(RS % 32 == BANK % 32, "bank padding");
+  static_assert(RS % 8 == 0 && XW % 8 == 0, "8-byte alignment of the tile rows");
+};
+
+// shared-memory offset of neighbour d of a site of basis b: the neighbour's
+// conventional cell is floor((beta_b + d)/2) away, its basis the parity of
+// beta_b + d.
+template <class C>
+__host__ __device__ constexpr int nbr_offset(int b, int dx, int dy, int dz) {
+  const int bx = basis_comp(C::KIND, b, 0), by = basis_comp(C::KIND, b, 1),
+            bz = basis_comp(C::KIND, b, 2);
+  const int cx = floordiv2(bx + dx), cy = floordiv2(by + dy), cz = floordiv2(bz + dz);
+  const int bp = basis_of_parity(C::KIND, (bx + dx) & 1, (by + dy) & 1, (bz + dz) & 1);
+  return cx + cy * C::RS + cz * C::PS + (bp - b) * C::XW;
+}
+
+template <class C, int B, int V>
+struct NbrOff {
+  static constexpr ShellVec v = shell_vec(C::KIND, V);
+  static constexpr int value = nbr_offset<C>(B, v.x, v.y, v.z);
+};
+
+// FCC partner-side decomposition: offset(b, d) = off0(d) + corr(b, class(d)),
+// class(d) = basis index of d's parity.
+template <class C, int V>
+struct Off0 {
+  static constexpr ShellVec v = shell_vec(C::KIND, V);
+  static constexpr int cls = basis_of_parity(C::KIND, v.x & 1, v.y & 1, v.z & 1);
+  static constexpr int value = nbr_offset<C>(0, v.x, v.y, v.z);
+};
+
+template <class C>
+__host__ __device__ constexpr int corr_of(int b, int cls) {
+  // any vector of class cls gives the same correction; use the parity vector itself
+  return nbr_offset<C>(b, basis_comp(C::KIND, cls, 0), basis_comp(C::KIND, cls, 1),
+                       basis_comp(C::KIND, cls, 2)) -
+         nbr_offset<C>(0, basis_comp(C::KIND, cls, 0), basis_comp(C::KIND, cls, 1),
+                       basis_comp(C::KIND, cls, 2));
+}
+
+// one-hot SWAR count of the species codes at base + offsets of shell vectors
+// [S, S + N)
+template <class C, int B, int S, int... I>
+__device__ __forceinline__ uint32_t count_i(const uint8_t* base, std::integer_sequence<int, I...>) {
+  return (0u + ... + (1u << base[NbrOff<C, B, S + I>::value]));
+}
+
+template <class C, int S, int... I>
+__device__ __forceinline__ uint32_t count_j_fcc(const uint8_t* const* cls_base,
+                                                std::integer_sequence<int, I...>) {
+  return (0u + ... + (1u << cls_base[Off0<C, S + I>::cls][Off0<C, S + I>::value]));
+}
+
+template <class C, int B, int... Ms>
+__device__ __forceinline__ void count_all_i(const uint8_t* base, uint32_t* acc,
+                                            std::integer_sequence<int, Ms...>) {
+  ((acc[Ms] = count_i<C, B, shell_start(C::KIND, Ms)>(
+        base, std::make_integer_sequence<int, shell_z(C::KIND, Ms)>{})),
+   ...);
+}
+
+template <class C, int... Ms>
+__device__ __forceinline__ void count_all_j_fcc(const uint8_t* const* cls_base, uint32_t* acc,
+                                                std::integer_sequence<int, Ms...>) {
+  ((acc[Ms] = count_j_fcc<C, shell_start(C::KIND, Ms)>(
+        cls_base, std::make_integer_sequence<int, shell_z(C::KIND, Ms)>{})),
+   ...);
+}
+
+struct BlockGeo {
+  int lo[3];    // tile origin in shifted conventional coordinates (includes halo)
+  int ext[3];   // tile extent
+  int g0[3];    // global coordinate of tile origin
+  int off;      // byte offset of tile x = 0 inside a sub-row (8-byte alignment)
+  bool wrap_x;  // the tile's x range crosses the periodic seam
+};
+
+__device__ __forceinline__ int cell_bound(int c, int n, int m) {
+  return static_cast<int>((static_cast<long long>(c) * n) / m);
+}
+
+__device__ __forceinline__ int wrapn(int v, int n) {
+  v %= n;
+  return v < 0 ? v + n : v;
+}
+
+template <class C>
+__global__ void __launch_bounds__(C::NT) k_sweep_tiled(const Geom g, const PhaseArgs a,
+                                                       const __grid_constant__ Tables tab,
+                                                       uint8_t* __restrict__ occ,
+                                                       const uint32_t* __restrict__ dtab,
+                                                       unsigned long long* __restrict__ stats) {
+  extern __shared__ __align__(16) uint8_t smem[];
+  uint32_t* s_tab = reinterpret_cast<uint32_t*>(smem);                       // 1536 words
+  uint32_t* s_d = s_tab + kTabWords;                                         // DROWS * ROWW
+  int* s_part = reinterpret_cast<int*>(s_d + C::DROWS * C::ROWW);            // NB * Z1
+  uint8_t* tile = smem + C::TILE_OFF;
+
+  const int tid = threadIdx.x;
+  const int bit[3] = {a.colour & 1, (a.colour >> 1) & 1, (a.colour >> 2) & 1};
+  const int A[3] = {g.m[0] / 2, g.m[1] / 2, g.m[2] / 2};
+  const int bidx[3] = {static_cast<int>(blockIdx.x), static_cast<int>(blockIdx.y),
+                       static_cast<int>(blockIdx.z)};
+  const int Bsz[3] = {C::BX, C::BY, C::BZ};
+
+  BlockGeo bg;
+  int a_first[3], a_last[3];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    a_first[d] = bidx[d] * Bsz[d];
+    a_last[d] = min(a_first[d] + Bsz[d], A[d]) - 1;
+    const int c0 = 2 * a_first[d] + bit[d], c1 = 2 * a_last[d] + bit[d];
+    bg.lo[d] = cell_bound(c0, g.n[d], g.m[d]) - C::H;
+    bg.ext[d] = cell_bound(c1 + 1, g.n[d], g.m[d]) + C::H - bg.lo[d];
+    bg.g0[d] = wrapn(bg.lo[d] + a.shift[d], g.n[d]);
+  }
+  bg.off = bg.g0[0] & 7;
+  bg.wrap_x = bg.g0[0] + bg.ext[0] > g.n[0];
+
+  // ---- tables ------------------------------------------------------------
+  for (int w = tid; w < kTabWords; w += C::NT) s_tab[w] = tab.w[w];
+  for (int w = tid; w < C::DROWS * C::ROWW; w += C::NT) s_d[w] = dtab[w];
+  for (int e = tid; e < C::NB * C::Z1; e += C::NT) {
+    const int b = e / C::Z1, dir = e % C::Z1;
+    const ShellVec v = shell_vec(C::KIND, dir);
+    const int off = nbr_offset<C>(b, v.x, v.y, v.z);
+    const int bj = basis_of_parity(C::KIND, (basis_comp(C::KIND, b, 0) + v.x) & 1,
+                                   (basis_comp(C::KIND, b, 1) + v.y) & 1,
+                                   (basis_comp(C::KIND, b, 2) + v.z) & 1);
+    s_part[e] = off * 4 + bj;
+  }
+
+  // ---- stage the tile ----------------------------------------------------
+  const int n_sub = bg.ext[1] * bg.ext[2] * C::G;  // device rows to copy
+  if (!bg.wrap_x) {
+    const int n8 = (bg.off + bg.ext[0] + 7) >> 3;
+    for (int item = tid; item < n_sub * n8; item += C::NT) {
+      const int chunk = item % n8;
+      const int sub = item / n8;
+      const int grp = sub % C::G;
+      const int ty = (sub / C::G) % bg.ext[1];
+      const int tz = sub / (C::G * bg.ext[1]);
+      const int gy = wrapn(bg.g0[1] + ty, g.n[1]);
+      const int gz = wrapn(bg.g0[2] + tz, g.n[2]);
+      const uint8_t* src = occ + dev_row(g, grp, gz, gy) + (bg.g0[0] - bg.off) + 8 * chunk;
+      const uint2 v = *reinterpret_cast<const uint2*>(src);
+      uint8_t* row = tile + tz * C::PS + ty * C::RS + 8 * chunk;
+      if constexpr (!C::PACK4) {
+        *reinterpret_cast<uint2*>(row + grp * C::XW) = v;
+      } else {
+        const uint2 lo = make_uint2((v.x & 0x0F0F0F0Fu) * C::W, (v.y & 0x0F0F0F0Fu) * C::W);
+        const uint2 hi = make_uint2(((v.x >> 4) & 0x0F0F0F0Fu) * C::W,
+                                    ((v.y >> 4) & 0x0F0F0F0Fu) * C::W);
+        *reinterpret_cast<uint2*>(row + (2 * grp) * C::XW) = lo;
+        *reinterpret_cast<uint2*>(row + (2 * grp + 1) * C::XW) = hi;
+      }
+    }
+  } else {
+    for (int item = tid; item < n_sub * bg.ext[0]; item += C::NT) {
+      const int tx = item % bg.ext[0];
+      const int sub = item / bg.ext[0];
+      const int grp = sub % C::G;
+      const int ty = (sub / C::G) % bg.ext[1];
+      const int tz = sub / (C::G * bg.ext[1]);
+      const int gx = wrapn(bg.g0[0] + tx, g.n[0]);
+      const int gy = wrapn(bg.g0[1] + ty, g.n[1]);
+      const int gz = wrapn(bg.g0[2] + tz, g.n[2]);
+      const uint8_t v = occ[dev_row(g, grp, gz, gy) + gx];
+      uint8_t* row = tile + tz * C::PS + ty * C::RS + bg.off + tx;
+      if constexpr (!C::PACK4) {
+        row[grp * C::XW] = v;
+      } else {
+        row[(2 * grp) * C::XW] = static_cast<uint8_t>((v & 15) * C::W);
+        row[(2 * grp + 1) * C::XW] = static_cast<uint8_t>((v >> 4) * C::W);
+      }
+    }
+  }
+  __syncthreads();
+
+  // ---- trials ------------------------------------------------------------
+  uint32_t n_att = 0, n_unl = 0, n_acc = 0;
+  int64_t sum_de = 0;
+  const int lane_a[3] = {tid % C::BX, (tid / C::BX) % C::BY, tid / (C::BX * C::BY)};
+  const int ac[3] = {a_first[0] + lane_a[0], a_first[1] + lane_a[1], a_first[2] + lane_a[2]};
+  if (ac[0] <= a_last[0] && ac[1] <= a_last[1] && ac[2] <= a_last[2]) {
+    int o[3], l[3], c[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      c[d] = 2 * ac[d] + bit[d];
+      const int b0 = cell_bound(c[d], g.n[d], g.m[d]);
+      o[d] = b0 - bg.lo[d];
+      l[d] = cell_bound(c[d] + 1, g.n[d], g.m[d]) - b0;
+    }
+    const uint32_t cid = (static_cast<uint32_t>(c[2]) * g.m[1] + c[1]) * g.m[0] + c[0];
+    n_att = static_cast<uint32_t>(l[0] * l[1] * l[2] * C::NB);
+
+    // global address of a tile byte offset (it includes bg.off; for storing
+    // accepted swaps)
+    auto store = [&](int toff, uint32_t code) {
+      const int tz = toff / C::PS;
+      const int r1 = toff - tz * C::PS;
+      const int ty = r1 / C::RS;
+      const int r2 = r1 - ty * C::RS;
+      const int b = r2 / C::XW;
+      const int tx = r2 - b * C::XW - bg.off;
+      int gx = bg.g0[0] + tx;
+      gx -= gx >= g.n[0] ? g.n[0] : 0;
+      int gy = bg.g0[1] + ty;
+      gy -= gy >= g.n[1] ? g.n[1] : 0;
+      int gz = bg.g0[2] + tz;
+      gz -= gz >= g.n[2] ? g.n[2] : 0;
+      if constexpr (!C::PACK4) {
+        occ[dev_row(g, b, gz, gy) + gx] = static_cast<uint8_t>(code);
+      } else {
+        uint8_t* p = occ + dev_row(g, b >> 1, gz, gy) + gx;
+        const uint32_t sig = (code * (C::W == 6 ? 43u : 52u)) >> 8;
+        const uint32_t sh = (b & 1) * 4u;
+        *p = static_cast<uint8_t>((*p & ~(15u << sh)) | (sig << sh));
+      }
+    };
+
+    auto attempt = [&](auto bconst, int ai, uint32_t wa, uint32_t wb) {
+      constexpr int B = decltype(bconst)::value;
+      const uint32_t dir = __umulhi(wa, static_cast<uint32_t>(C::Z1));
+      const int pt = s_part[B * C::Z1 + dir];
+      const int aj = ai + (pt >> 2);
+      const uint32_t p = tile[ai], q = tile[aj];
+      uint32_t acc_i[C::M], acc_j[C::M];
+      count_all_i<C, B>(tile + ai, acc_i, std::make_integer_sequence<int, C::M>{});
+      if constexpr (C::KIND == 0) {
+        count_all_i<C, 1 - B>(tile + aj, acc_j, std::make_integer_sequence<int, C::M>{});
+      } else {
+        const int bj = pt & 3;
+        const uint8_t* cls_base[4];
+#pragma unroll
+        for (int cl = 0; cl < 4; ++cl) {
+          const int c01 = (bj & 1) ? corr_of<C>(1, cl) : corr_of<C>(0, cl);
+          const int c23 = (bj & 1) ? corr_of<C>(3, cl) : corr_of<C>(2, cl);
+          cls_base[cl] = tile + aj + ((bj & 2) ? c23 : c01);
+        }
+        count_all_j_fcc<C>(cls_base, acc_j, std::make_integer_sequence<int, C::M>{});
+      }
+      if (p == q) return;
+      ++n_unl;
+      const uint32_t* row = s_d + (p * C::KMAX + q) * C::ROWW;
+      int64_t de = -static_cast<int64_t>((static_cast<uint64_t>(row[C::ROWW - 1]) << 32) |
+                                         row[C::ROWW - 2]);
+#pragma unroll
+      for (int m = 0; m < C::M; ++m) {
+        if constexpr (C::KMAX <= 5) {
+          const uint32_t F = 0x20820820u + acc_i[m] - acc_j[m];  // bias 32 in each 6-bit field
+#pragma unroll
+          for (int s = 1; s < C::KMAX; ++s)
+            de += static_cast<int64_t>((F >> (6 * s)) & 63u) *
+                  static_cast<int32_t>(row[m * (C::KMAX - 1) + s - 1]);
+        } else {
+#pragma unroll
+          for (int s = 1; s < C::KMAX; ++s)
+            de += static_cast<int64_t>(static_cast<int>((acc_i[m] >> (5 * s)) & 31u) -
+                                       static_cast<int>((acc_j[m] >> (5 * s)) & 31u)) *
+                  static_cast<int32_t>(row[m * (C::KMAX - 1) + s - 1]);
+        }
+      }
+      bool ok;
+      if (de <= 0) {
+        ok = true;
+      } else if (a.mode == kModeZeroT) {
+        ok = false;
+      } else if (a.mode == kModeAcceptAll) {
+        ok = true;
+      } else {
+        const uint64_t idx = static_cast<uint64_t>(de) >> a.s;
+        ok = idx < (1ull << 27) &&
+             wb < compose_threshold(s_tab[idx & 511u], s_tab[512 + ((idx >> 9) & 511u)],
+                                    s_tab[1024 + (idx >> 18)]);
+      }
+      if (ok) {
+        tile[ai] = static_cast<uint8_t>(q);
+        tile[aj] = static_cast<uint8_t>(p);
+        store(ai, q);
+        store(aj, p);
+        ++n_acc;
+        sum_de += de;
+      }
+    };
+
+    for (int zr = 0; zr < l[2]; ++zr)
+      for (int yr = 0; yr < l[1]; ++yr) {
+        const int rb = bg.off + (o[2] + zr) * C::PS + (o[1] + yr) * C::RS + o[0];
+        for (int xr = 0; xr < l[0]; ++xr) {
+          const uint32_t cc = static_cast<uint32_t>((zr * l[1] + yr) * l[0] + xr);
+          const int ai = rb + xr;
+          const U4 w0 = philox4x32_10(cc * (C::NB / 2), cid, a.t, 0u, g.seed_lo, g.seed_hi);
+          attempt(std::integral_constant<int, 0>{}, ai, w0.x, w0.y);
+          attempt(std::integral_constant<int, 1>{}, ai + C::XW, w0.z, w0.w);
+          if constexpr (C::NB == 4) {
+            const U4 w1 = philox4x32_10(cc * 2 + 1, cid, a.t, 0u, g.seed_lo, g.seed_hi);
+            attempt(std::integral_constant<int, 2>{}, ai + 2 * C::XW, w1.x, w1.y);
+            attempt(std::integral_constant<int, 3>{}, ai + 3 * C::XW, w1.z, w1.w);
+          }
+        }
+      }
+  }
+  warp_reduce_add_stats(stats, n_att, n_unl, n_acc, sum_de);
+}
+
+template <class C>
+size_t smem_bytes(int ext_z) {
+  return static_cast<size_t>(C::TILE_OFF) + static_cast<size_t>(C::PS) * ext_z;
+}
+
+// cells of colour bit `bit` along one dimension: the largest tile extent of
+// any block (for the dynamic shared-memory size)
+inline int max_extent(int n, int m, int bsz, int halo) {
+  const int A = m / 2;
+  int best = 0;
+  for (int bit = 0; bit < 2; ++bit)
+    for (int a0 = 0; a0 < A; a0 += bsz) {
+      const int a1 = (a0 + bsz < A ? a0 + bsz : A) - 1;
+      const int c0 = 2 * a0 + bit, c1 = 2 * a1 + bit;
+      const int lo = static_cast<int>((static_cast<long long>(c0) * n) / m) - halo;
+      const int hi = static_cast<int>((static_cast<long long>(c1 + 1) * n) / m) + halo;
+      best = hi - lo > best ? hi - lo : best;
+    }
+  return best;
+}
+
+template <class C>
+bool supported(const Geom& g) {
+  if (g.kind != C::KIND || g.M != C::M || g.L != C::L || g.pack4 != (C::PACK4 ? 1 : 0)) return false;
+  if (g.K > C::KMAX || code_width(g.K) != (g.pack4 ? code_width(g.K) : C::W)) return false;
+  if (C::KMAX == 6 && g.K != 6) return false;
+  const int Bsz[3] = {C::BX, C::BY, C::BZ};
+  const int EXT[3] = {C::EXT_X, C::EXT_Y, C::EXT_Z};
+  for (int d = 0; d < 3; ++d) {
+    if (g.m[d] < 4) return false;
+    if (g.m[d] / 2 < Bsz[d] + 1) return false;  // a tile never wraps onto itself
+    if (max_extent(g.n[d], g.m[d], Bsz[d], C::H) > EXT[d]) return false;
+  }
+  return smem_bytes<C>(max_extent(g.n[2], g.m[2], C::BZ, C::H)) <= 227 * 1024;
+}
+
+template <class C>
+cudaError_t launch_cfg(const Geom& g, const PhaseArgs& a, const Tables& tab, uint8_t* occ,
+                       const TiledEpi& epi, unsigned long long* stats, cudaStream_t st) {
+  const int ext_z = max_extent(g.n[2], g.m[2], C::BZ, C::H);
+  const size_t smem = smem_bytes<C>(ext_z);
+  cudaError_t e = cudaFuncSetAttribute(k_sweep_tiled<C>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       static_cast<int>(smem));
+  if (e != cudaSuccess) return e;
+  const dim3 grid((g.m[0] / 2 + C::BX - 1) / C::BX, (g.m[1] / 2 + C::BY - 1) / C::BY,
+                  (g.m[2] / 2 + C::BZ - 1) / C::BZ);
+  k_sweep_tiled<C><<<grid, C::NT, smem, st>>>(g, a, tab, occ, epi.d_table, stats);
+  return cudaGetLastError();
+}
+
+}  // namespace tiled
+}  // namespace smcx

@@ -73,19 +73,26 @@ uint64_t n_sites(const smcx_lattice_desc* d) {
 
 size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
+size_t row_pitch(const smcx_lattice_desc* d) { return align_up(d->n[0], 16); }
+
+// device storage: [group][z][y] rows of row_pitch bytes (see Geom in
+// smcx_common.cuh); groups = basis sites (8-bit) or basis pairs (4-bit)
 size_t occ_bytes(const smcx_lattice_desc* d) {
-  const uint64_t N = n_sites(d);
-  const uint64_t raw = d->pack_bits == 4 ? (N + 1) / 2 : N;
-  return align_up(static_cast<size_t>(raw), 16);
+  const size_t nb = static_cast<size_t>(basis_count(static_cast<int>(d->kind)));
+  const size_t groups = d->pack_bits == 4 ? nb / 2 : nb;
+  return groups * d->n[2] * d->n[1] * row_pitch(d);
 }
 
 struct WorkLayout {
-  size_t stats;   // 16 x u64: call stats, cumulative stats, status
-  size_t V;       // [4][K][K] int64
-  size_t D;       // difference table for the tiled kernel
-  size_t pairs;   // [4][K][K] u64
+  size_t stats;    // 16 x u64: call stats, cumulative stats, status/flags
+  size_t V;        // [4][K][K] int64
+  size_t D;        // per-(p, q) difference rows of the tiled kernel
+  size_t pairs;    // [4][K][K] u64
+  size_t scratch;  // N bytes: canonical occupancy in transit
   size_t total;
 };
+
+constexpr size_t kTiledTableWords = 6 * 5 * 6 * 22;  // largest DROWS * ROWW (K = 6, M = 4)
 
 WorkLayout work_layout(const smcx_lattice_desc* d) {
   const size_t K = d->n_species;
@@ -93,9 +100,10 @@ WorkLayout work_layout(const smcx_lattice_desc* d) {
   w.stats = 0;
   w.V = 256;
   w.D = w.V + align_up(sizeof(int64_t) * kMaxShells * K * K, 256);
-  const size_t kd = K <= 16 ? K : 0;
-  w.pairs = w.D + align_up(sizeof(int64_t) * kMaxShells * kd * kd * kd + 16, 256);
-  w.total = w.pairs + align_up(sizeof(uint64_t) * kMaxShells * K * K, 256);
+  w.pairs = w.D + align_up(sizeof(uint32_t) * kTiledTableWords, 256);
+  const size_t kp = K < 6 ? 6 : K;  // the tiled pair count writes [4][6][6] at most
+  w.scratch = w.pairs + align_up(sizeof(uint64_t) * kMaxShells * kp * kp, 256);
+  w.total = w.scratch + align_up(static_cast<size_t>(n_sites(d)), 256);
   return w;
 }
 
@@ -182,12 +190,17 @@ struct smcx_lattice {
   int opt_kernel = 0;
   int opt_tile = -1;
   int n_sm = 0;
+  bool tiled_table_ok = false;  // the tiled kernel's int32 difference table fits
+  int tiled_kmax = 0;
 
   unsigned long long* stats() { return reinterpret_cast<unsigned long long*>(d_work + wl.stats); }
   int64_t* dV() { return reinterpret_cast<int64_t*>(d_work + wl.V); }
   unsigned long long* pairs() {
     return reinterpret_cast<unsigned long long*>(d_work + wl.pairs);
   }
+  uint8_t* scratch() { return d_work + wl.scratch; }
+  uint32_t* dtab() { return reinterpret_cast<uint32_t*>(d_work + wl.D); }
+  unsigned int* flag() { return reinterpret_cast<unsigned int*>(stats() + kStatStatus); }
   Geom geom() const {
     Geom g;
     g.kind = static_cast<int>(desc.kind);
@@ -201,6 +214,8 @@ struct smcx_lattice {
     g.M = static_cast<int>(M);
     g.z1 = shell_z(g.kind, 0);
     g.pack4 = desc.pack_bits == 4;
+    g.px = static_cast<int>(row_pitch(&desc));
+    g.W = desc.pack_bits == 4 ? 1 : code_width(g.K);
     g.seed_lo = static_cast<uint32_t>(desc.seed);
     g.seed_hi = static_cast<uint32_t>(desc.seed >> 32);
     return g;
@@ -264,47 +279,65 @@ smcx_status validate_occupancy(const smcx_lattice_desc& d, const uint8_t* h) {
   return SMCX_OK;
 }
 
-// canonical bytes -> device storage (packed: site i in nibble i&1 of byte i>>1)
+// canonical host bytes -> workspace scratch -> (validated on the device) ->
+// device storage
 smcx_status upload_occupancy(smcx_lattice* lat, const uint8_t* h) {
-  const size_t bytes = occ_bytes(&lat->desc);
-  if (lat->desc.pack_bits == 8) {
-    SMCX_CUDA(lat, cudaMemsetAsync(lat->d_occ, 0, bytes, lat->stream));
-    SMCX_CUDA(lat, cudaMemcpyAsync(lat->d_occ, h, lat->N, cudaMemcpyHostToDevice, lat->stream));
-    SMCX_CUDA(lat, cudaStreamSynchronize(lat->stream));
-    return SMCX_OK;
-  }
-  std::vector<uint8_t> packed(bytes, 0);
-  for (uint64_t i = 0; i < lat->N; ++i) packed[i >> 1] |= static_cast<uint8_t>(h[i] << ((i & 1) * 4));
-  SMCX_CUDA(lat, cudaMemcpyAsync(lat->d_occ, packed.data(), bytes, cudaMemcpyHostToDevice,
+  const Geom g = lat->geom();
+  const uint32_t n_cells = static_cast<uint32_t>(lat->N / lat->nb);
+  SMCX_CUDA(lat, cudaMemcpyAsync(lat->scratch(), h, lat->N, cudaMemcpyHostToDevice, lat->stream));
+  SMCX_CUDA(lat, cudaMemsetAsync(lat->flag(), 0, sizeof(unsigned int), lat->stream));
+  SMCX_CUDA(lat, launch_validate(lat->scratch(), lat->N, lat->desc.n_species, lat->flag(),
+                                 lat->n_sm, lat->stream));
+  unsigned int bad = 0;
+  SMCX_CUDA(lat, cudaMemcpyAsync(&bad, lat->flag(), sizeof(bad), cudaMemcpyDeviceToHost,
                                  lat->stream));
+  SMCX_CUDA(lat, cudaStreamSynchronize(lat->stream));
+  if (bad) return fail(SMCX_EINVAL, "species id >= n_species in occupancy");
+  SMCX_CUDA(lat, cudaMemsetAsync(lat->d_occ, 0, occ_bytes(&lat->desc), lat->stream));
+  SMCX_CUDA(lat, launch_canon_to_dev(g, lat->scratch(), lat->d_occ, n_cells, lat->n_sm,
+                                     lat->stream));
   SMCX_CUDA(lat, cudaStreamSynchronize(lat->stream));
   return SMCX_OK;
 }
 
 smcx_status download_occupancy(smcx_lattice* lat, uint8_t* h) {
-  if (lat->desc.pack_bits == 8) {
-    SMCX_CUDA(lat, cudaMemcpyAsync(h, lat->d_occ, lat->N, cudaMemcpyDeviceToHost, lat->stream));
-    SMCX_CUDA(lat, cudaStreamSynchronize(lat->stream));
-    return SMCX_OK;
-  }
-  std::vector<uint8_t> packed(occ_bytes(&lat->desc));
-  SMCX_CUDA(lat, cudaMemcpyAsync(packed.data(), lat->d_occ, packed.size(), cudaMemcpyDeviceToHost,
-                                 lat->stream));
+  const Geom g = lat->geom();
+  const uint32_t n_cells = static_cast<uint32_t>(lat->N / lat->nb);
+  SMCX_CUDA(lat, launch_dev_to_canon(g, lat->d_occ, lat->scratch(), n_cells, lat->n_sm,
+                                     lat->stream));
+  SMCX_CUDA(lat, cudaMemcpyAsync(h, lat->scratch(), lat->N, cudaMemcpyDeviceToHost, lat->stream));
   SMCX_CUDA(lat, cudaStreamSynchronize(lat->stream));
-  for (uint64_t i = 0; i < lat->N; ++i) h[i] = (packed[i >> 1] >> ((i & 1) * 4)) & 15;
   return SMCX_OK;
 }
 
 smcx_status run_pair_counts(smcx_lattice* lat, uint32_t n_shells, std::vector<uint64_t>* out) {
   const size_t K = lat->desc.n_species;
   const size_t n_cnt = n_shells * K * K;
-  SMCX_CUDA(lat, cudaMemsetAsync(lat->pairs(), 0, sizeof(uint64_t) * n_cnt, lat->stream));
   Geom g = lat->geom();
+  out->assign(n_cnt, 0);
+  if (K <= 6) {
+    // tiled half-shell counts H (rows of KMAX species); N = H + H^T
+    const size_t kmax = K <= 5 ? 5 : 6;
+    const int ms = n_shells < 2 ? 2 : static_cast<int>(n_shells);
+    const size_t n_h = static_cast<size_t>(ms) * kmax * kmax;
+    SMCX_CUDA(lat, cudaMemsetAsync(lat->pairs(), 0, sizeof(uint64_t) * n_h, lat->stream));
+    SMCX_CUDA(lat, launch_pair_count_tiled(g, static_cast<int>(n_shells), lat->d_occ, lat->pairs(),
+                                           lat->n_sm, lat->stream, false));
+    std::vector<uint64_t> h(n_h);
+    SMCX_CUDA(lat, cudaMemcpyAsync(h.data(), lat->pairs(), sizeof(uint64_t) * n_h,
+                                   cudaMemcpyDeviceToHost, lat->stream));
+    SMCX_CUDA(lat, cudaStreamSynchronize(lat->stream));
+    for (size_t m = 0; m < n_shells; ++m)
+      for (size_t a = 0; a < K; ++a)
+        for (size_t b = 0; b < K; ++b)
+          (*out)[(m * K + a) * K + b] = h[(m * kmax + a) * kmax + b] + h[(m * kmax + b) * kmax + a];
+    return SMCX_OK;
+  }
+  SMCX_CUDA(lat, cudaMemsetAsync(lat->pairs(), 0, sizeof(uint64_t) * n_cnt, lat->stream));
   const ShellParam sp = shell_param(g.kind);
   SMCX_CUDA(lat, launch_pair_count_generic(g, sp, static_cast<int>(n_shells), lat->d_occ,
-                                           lat->pairs(), static_cast<uint32_t>(lat->N), lat->n_sm,
-                                           lat->stream));
-  out->assign(n_cnt, 0);
+                                           lat->pairs(), static_cast<uint32_t>(lat->N / lat->nb),
+                                           lat->n_sm, lat->stream));
   SMCX_CUDA(lat, cudaMemcpyAsync(out->data(), lat->pairs(), sizeof(uint64_t) * n_cnt,
                                  cudaMemcpyDeviceToHost, lat->stream));
   SMCX_CUDA(lat, cudaStreamSynchronize(lat->stream));
@@ -344,14 +377,82 @@ smcx_status restart_running_energy(smcx_lattice* lat) {
 }
 
 // one colour phase of the current sweep
+int tiled_shape_for(smcx_lattice* lat) {
+  const Geom g = lat->geom();
+  if (!lat->tiled_table_ok) return -1;
+  if (lat->opt_tile >= 0) return tiled_supported(g, lat->opt_tile) ? lat->opt_tile : -1;
+  for (int sh = 0; sh < tiled_shape_count(g.kind); ++sh)
+    if (tiled_supported(g, sh)) return sh;
+  return -1;
+}
+
+// which kernel a colour phase runs: 1 = generic, 2 = tiled
+int kernel_choice(smcx_lattice* lat) {
+  if (lat->opt_kernel == 1) return 1;
+  return tiled_shape_for(lat) >= 0 ? 2 : 1;
+}
+
+// one colour phase of the current sweep
 smcx_status launch_colour(smcx_lattice* lat, int colour, const PhaseArgs& base, const Tables& tab) {
   PhaseArgs a = base;
   a.colour = colour;
   const Geom g = lat->geom();
+  for (int d = 0; d < 3; ++d)
+    if (g.m[d] == 1 && ((colour >> d) & 1)) return SMCX_OK;  // no cell of this colour
+  const int kern = kernel_choice(lat);
+  if (lat->opt_kernel == 2 && kern != 2)
+    return fail(SMCX_EINVAL, "the tiled kernel does not support this lattice/EPI/tile shape");
+  if (kern == 2) {
+    TiledEpi te;
+    te.kmax = lat->tiled_kmax;
+    te.row_words = tiled_row_words(g.M, te.kmax);
+    te.n_rows = te.kmax * code_width(g.K) * te.kmax;
+    te.d_table = lat->dtab();
+    SMCX_CUDA(lat, launch_sweep_tiled(g, a, tab, lat->d_occ, te, lat->stats(), tiled_shape_for(lat),
+                                      lat->stream));
+    return SMCX_OK;
+  }
   const ShellParam sp = shell_param(g.kind);
   SMCX_CUDA(lat, launch_sweep_generic(g, a, sp, tab, lat->d_occ, lat->dV(), lat->stats(),
                                       lat->stream));
   return SMCX_OK;
+}
+
+// Difference rows of the tiled kernel, one per pair of species codes
+// (code = sigma * W, row = code_p * KMAX + code_q): D'_{m,s} = D_{m,s} - D_{m,0}
+// for s = 1..K-1 with D_{m,s} = V_m(q,s) - V_m(p,s), then the int64 constant
+// C = [32 sum_{m,s} D'_{m,s} when K <= 5] + D_{1,q} - D_{1,p}.  Returns false
+// when a D' does not fit int32.
+bool build_tiled_table(smcx_lattice* lat, std::vector<uint32_t>* out) {
+  const int K = static_cast<int>(lat->desc.n_species);
+  const int M = static_cast<int>(lat->M);
+  if (K > 6 || M < 2) return false;
+  const int kmax = K <= 5 ? 5 : 6;
+  const int W = code_width(K);
+  const int roww = tiled_row_words(M, kmax);
+  out->assign(static_cast<size_t>(kmax) * W * kmax * roww, 0u);
+  auto V = [&](int m, int a, int b) { return lat->V[(static_cast<size_t>(m) * K + a) * K + b]; };
+  for (int p = 0; p < K; ++p)
+    for (int q = 0; q < K; ++q) {
+      uint32_t* row = out->data() + (static_cast<size_t>(p * W) * kmax + q * W) * roww;
+      __int128 C = 0;
+      for (int m = 0; m < M; ++m) {
+        const int64_t d0 = V(m, q, 0) - V(m, p, 0);
+        for (int s = 1; s < K; ++s) {
+          const int64_t dp = (V(m, q, s) - V(m, p, s)) - d0;
+          if (dp > INT32_MAX || dp < INT32_MIN) return false;
+          row[m * (kmax - 1) + s - 1] = static_cast<uint32_t>(static_cast<int32_t>(dp));
+          if (kmax == 5) C += static_cast<__int128>(32) * dp;
+        }
+      }
+      C += (V(0, q, q) - V(0, p, q)) - (V(0, q, p) - V(0, p, p));
+      if (C > INT64_MAX || C < INT64_MIN) return false;
+      const uint64_t c64 = static_cast<uint64_t>(static_cast<int64_t>(C));
+      row[roww - 2] = static_cast<uint32_t>(c64);
+      row[roww - 1] = static_cast<uint32_t>(c64 >> 32);
+    }
+  lat->tiled_kmax = kmax;
+  return true;
 }
 
 smcx_status read_call_stats(smcx_lattice* lat, smcx_sweep_stats* out) {
@@ -400,8 +501,7 @@ smcx_status smcx_create_lattice(const smcx_lattice_desc* desc, void* d_occ, void
   if (!d_occ || !d_work || !h_init) return fail(SMCX_EINVAL, "null buffer");
   if (reinterpret_cast<uintptr_t>(d_occ) % 16 != 0 || reinterpret_cast<uintptr_t>(d_work) % 256 != 0)
     return fail(SMCX_EINVAL, "occupancy must be 16-byte and workspace 256-byte aligned");
-  smcx_status s = validate_occupancy(*desc, h_init);
-  if (s != SMCX_OK) return s;
+  smcx_status s = SMCX_OK;
   auto* lat = new smcx_lattice();
   lat->desc = *desc;
   lat->nb = basis_count(static_cast<int>(desc->kind));
@@ -448,6 +548,11 @@ smcx_status smcx_set_epi(smcx_lattice* lat, uint32_t n_shells, const int64_t* v_
   std::copy(lat->V.begin(), lat->V.end(), vpad.begin());
   SMCX_CUDA(lat, cudaMemcpyAsync(lat->dV(), vpad.data(), sizeof(int64_t) * vpad.size(),
                                  cudaMemcpyHostToDevice, lat->stream));
+  std::vector<uint32_t> dtab;
+  lat->tiled_table_ok = build_tiled_table(lat, &dtab);
+  if (lat->tiled_table_ok)
+    SMCX_CUDA(lat, cudaMemcpyAsync(lat->dtab(), dtab.data(), sizeof(uint32_t) * dtab.size(),
+                                   cudaMemcpyHostToDevice, lat->stream));
   SMCX_CUDA(lat, cudaStreamSynchronize(lat->stream));
   lat->has_epi = true;
   s = restart_running_energy(lat);
@@ -568,8 +673,6 @@ smcx_status smcx_set_occupancy(smcx_lattice* lat, const uint8_t* h_in) {
   smcx_status s = check_handle(lat);
   if (s != SMCX_OK) return s;
   if (!h_in) return fail(SMCX_EINVAL, "null input");
-  s = validate_occupancy(lat->desc, h_in);
-  if (s != SMCX_OK) return s;
   s = upload_occupancy(lat, h_in);
   if (s != SMCX_OK) return s;
   return restart_running_energy(lat);
@@ -701,15 +804,25 @@ smcx_status smcx_set_option(smcx_lattice* lat, uint32_t key, int64_t value) {
 }
 
 uint32_t smcx_tile_shape_count(uint32_t kind) {
-  (void)kind;
-  return 0;
+  if (kind > 1) return 0;
+  return static_cast<uint32_t>(tiled_shape_count(static_cast<int>(kind)));
 }
 
 smcx_status smcx_tile_shape(uint32_t kind, uint32_t i, uint32_t* cells_xyz) {
-  (void)kind;
-  (void)i;
-  (void)cells_xyz;
-  return fail(SMCX_EINVAL, "no tile shapes");
+  if (kind > 1 || !cells_xyz || i >= smcx_tile_shape_count(kind))
+    return fail(SMCX_EINVAL, "bad tile shape request");
+  int c[3];
+  tiled_shape_cells(static_cast<int>(kind), static_cast<int>(i), c);
+  for (int d = 0; d < 3; ++d) cells_xyz[d] = static_cast<uint32_t>(c[d]);
+  return SMCX_OK;
+}
+
+smcx_status smcx_kernel_in_use(smcx_lattice* lat, uint32_t* kernel, int32_t* tile_shape) {
+  if (!lat || !kernel || !tile_shape) return fail(SMCX_EINVAL, "null argument");
+  if (!lat->has_epi) return fail(SMCX_ESTATE, "no EPI set");
+  *kernel = static_cast<uint32_t>(kernel_choice(lat));
+  *tile_shape = *kernel == 2 ? tiled_shape_for(lat) : -1;
+  return SMCX_OK;
 }
 
 smcx_status smcx_destroy(smcx_lattice* lat) {

@@ -130,6 +130,15 @@ __host__ __device__ __forceinline__ uint32_t compose_threshold(uint32_t t0, uint
 // ---------------------------------------------------------------------------
 // Launch parameters.
 // ---------------------------------------------------------------------------
+// Device storage of the occupancy (internal; the C ABI exchanges the
+// canonical layout).  Rows of px bytes (n_x rounded up to 16) ordered
+// [group][z][y]:
+//   8-bit: group = basis site b, byte x holds the code sigma * W of site
+//          (x, y, z, b) -- W is the field width of the one-hot species
+//          counters of the tiled sweep (6 for K <= 5, 5 for K = 6, 1 above);
+//   4-bit: group = basis pair b/2, byte x holds sigma of b even in the low
+//          and of b odd in the high nibble (both sites of one conventional
+//          cell, so no two link cells ever write one byte).
 struct Geom {
   int kind, nb;
   int n[3];
@@ -138,8 +147,16 @@ struct Geom {
   int K, M;       // species, shells in use
   int z1;         // first-shell coordination
   int pack4;      // occupancy stored two sites per byte
+  int px;         // device row pitch in bytes (multiple of 16)
+  int W;          // code multiplier of 8-bit storage
   uint32_t seed_lo, seed_hi;
 };
+
+__host__ __device__ inline int code_width(int K) { return K <= 5 ? 6 : (K == 6 ? 5 : 1); }
+
+__host__ __device__ inline size_t dev_row(const Geom& g, int grp, int z, int y) {
+  return ((static_cast<size_t>(grp) * g.n[2] + z) * g.n[1] + y) * static_cast<size_t>(g.px);
+}
 
 struct PhaseArgs {
   uint32_t t;      // global sweep index

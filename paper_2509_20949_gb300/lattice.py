@@ -146,6 +146,12 @@ class Lattice:
         check(self.L.smcx_get_layout(self.h, ctypes.byref(L), m))
         return int(L.value), tuple(int(v) for v in m)
 
+    def kernel_in_use(self):
+        k = ctypes.c_uint32()
+        sh = ctypes.c_int32()
+        check(self.L.smcx_kernel_in_use(self.h, ctypes.byref(k), ctypes.byref(sh)))
+        return int(k.value), int(sh.value)
+
     def checkpoint(self) -> bytes:
         n = ctypes.c_size_t()
         check(self.L.smcx_checkpoint(self.h, None, ctypes.byref(n)))

@@ -61,11 +61,16 @@ def write_region_sites(orc, desc, t, cids):
 
 
 def colour_cells(orc, desc, colour):
+    """Ascending ids of the link cells of one colour."""
     L, m = orc.layout(desc)
-    cids = []
-    for cz in range(m[2]):
-        for cy in range(m[1]):
-            for cx in range(m[0]):
-                if ((cx & 1) | ((cy & 1) << 1) | ((cz & 1) << 2)) == colour:
-                    cids.append((cz * m[1] + cy) * m[0] + cx)
-    return np.array(cids, dtype=np.uint32)
+    axes = []
+    for d in range(3):
+        bit = (colour >> d) & 1
+        if m[d] == 1:
+            if bit:
+                return np.zeros(0, dtype=np.uint32)
+            axes.append(np.zeros(1, dtype=np.int64))
+        else:
+            axes.append(np.arange(bit, m[d], 2, dtype=np.int64))
+    cid = (axes[2][:, None, None] * m[1] + axes[1][None, :, None]) * m[0] + axes[0][None, None, :]
+    return cid.ravel().astype(np.uint32)

@@ -64,10 +64,11 @@ def test_host_philox_agrees_with_oracle(L, orc):
 def test_buffer_sizes_and_validation(L):
     d = make_desc(0, (16, 16, 16), 4)
     ob = L.smcx_occupancy_bytes(ctypes.byref(d))
-    assert ob == 8192 and ob % 16 == 0
-    assert L.smcx_workspace_bytes(ctypes.byref(d)) >= 256
+    assert ob >= 8192 and ob % 16 == 0
+    assert L.smcx_workspace_bytes(ctypes.byref(d)) >= 256 + 8192
     d4 = make_desc(0, (3, 3, 3), 4, pack_bits=4)
-    assert L.smcx_occupancy_bytes(ctypes.byref(d4)) == 32
+    assert 27 <= L.smcx_occupancy_bytes(ctypes.byref(d4)) and \
+        L.smcx_occupancy_bytes(ctypes.byref(d4)) % 16 == 0
     for bad in (make_desc(2, (4, 4, 4), 4), make_desc(0, (0, 4, 4), 4), make_desc(0, (4, 4, 4), 0),
                 make_desc(0, (4, 4, 4), 17, pack_bits=4), make_desc(0, (4, 4, 4), 4, pack_bits=2),
                 make_desc(0, (2048, 2048, 1024), 4), make_desc(0, (4, 4, 4), 4, flags=64)):
