@@ -27,8 +27,6 @@ cudaError_t launch_philox_fill(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c
 // Per-(p, q) rows of the energy-difference table used by the tiled kernel.
 struct TiledEpi {
   int kmax;        // 5 or 6 (species classes compiled)
-  int row_words;   // 32-bit words per (code_p, code_q) row
-  int n_rows;      // rows in the table
   const uint32_t* d_table;
 };
 
@@ -41,8 +39,21 @@ bool tiled_supported(const Geom& g, int shape);
 int tiled_shape_count(int kind);
 void tiled_shape_cells(int kind, int shape, int cells[3]);
 
-// table layout helpers shared by the host table builder and the kernel
-int tiled_row_words(int M, int kmax);
+// Layout of the tiled kernel's difference rows, shared by the host table
+// builder and the kernel: row (sigma_p, sigma_q) at byte
+// (sigma_p * kmax + sigma_q) * tiled_row_bytes, int32 D'[m][s - 1] at its
+// start and the int64 constant C at tiled_doff_c.
+__host__ __device__ constexpr int tiled_code_width(int kmax) { return kmax <= 5 ? 6 : 5; }
+__host__ __device__ constexpr int tiled_doff_c(int M, int kmax) {
+  return (4 * M * (kmax - 1) + 7) / 8 * 8;
+}
+// rows are 16-byte aligned (vector loads): rstep * W must be a multiple of 16
+__host__ __device__ constexpr int tiled_row_bytes(int M, int kmax) {
+  const int W = tiled_code_width(kmax);
+  const int q = W == 6 ? 8 : 16;
+  const int rstep = ((tiled_doff_c(M, kmax) + 8 + W - 1) / W + q - 1) / q * q;
+  return rstep * W;
+}
 
 }  // namespace smcx
 

@@ -59,15 +59,16 @@ __host__ __device__ constexpr int shell_reach_c(int kind, int M) {
   return r;
 }
 
-template <int KIND_, int M_, int KMAX_, bool PACK4_, int BX_, int BY_, int BZ_>
+template <int KIND_, int M_, int KMAX_, bool PACK4_, int BX_, int BY_, int BZ_, bool RAGGED_>
 struct Cfg {
   static constexpr int KIND = KIND_, M = M_, KMAX = KMAX_, BX = BX_, BY = BY_, BZ = BZ_;
-  static constexpr bool PACK4 = PACK4_;
+  static constexpr bool PACK4 = PACK4_, RAGGED = RAGGED_;
   static constexpr int NB = KIND == 0 ? 2 : 4;
   static constexpr int HR = shell_reach_c(KIND, M);
   static constexpr int L = (1 + HR) / 2 + 1;   // link-cell edge (conventional cells)
   static constexpr int H = 2;                  // halo: reads reach 1 + h_R <= 4 half units
-  static constexpr int SLACK = 2 * L - 1;      // cells of edge L+1 in a ragged dimension
+  // cells of edge L+1 in a ragged dimension (none when every edge is L)
+  static constexpr int SLACK = RAGGED ? 2 * L - 1 : 0;
   static constexpr int EXT_X = (2 * BX - 1) * L + SLACK + 2 * H;
   static constexpr int EXT_Y = (2 * BY - 1) * L + SLACK + 2 * H;
   static constexpr int EXT_Z = (2 * BZ - 1) * L + SLACK + 2 * H;
@@ -80,12 +81,16 @@ struct Cfg {
   static constexpr int NT = BX * BY * BZ;
   static constexpr int Z1 = shell_z(KIND, 0);
   static constexpr int NV = shell_start(KIND, M);
-  static constexpr int ROWW = round_up(M * (KMAX - 1) + 2, 2);  // D' words + C (int64)
-  static constexpr int CODES = KMAX * W;                          // rows indexed by codes
-  static constexpr int DROWS = CODES * KMAX;                      // code_p*KMAX + code_q
+  // difference rows: int32 D'[m][s-1] then the int64 constant C at DOFF_C;
+  // row (sigma_p, sigma_q) starts at byte (code_p * KMAX + code_q) * RSTEP,
+  // i.e. at (sigma_p * KMAX + sigma_q) * ROWB, so codes index it directly
+  static constexpr int DOFF_C = tiled_doff_c(M, KMAX);
+  static constexpr int ROWB = tiled_row_bytes(M, KMAX);
+  static constexpr int RSTEP = ROWB / W;
+  static constexpr int DBYTES = KMAX * KMAX * ROWB;
   static constexpr int G = PACK4 ? NB / 2 : NB;                   // device row groups
   static constexpr int TILE_OFF =
-      round_up(4 * (kTabWords + DROWS * ROWW + NB * Z1), 16);     // shared bytes before the tile
+      round_up(4 * kTabWords + DBYTES + 4 * NB * Z1, 16);         // shared bytes before the tile
   static_assert(RS % 32 == BANK % 32, "bank padding");
   static_assert(RS % 8 == 0 && XW % 8 == 0, "8-byte alignment of the tile rows");
 };
@@ -127,45 +132,56 @@ __host__ __device__ constexpr int corr_of(int b, int cls) {
 }
 
 // one-hot SWAR count of the species codes at base + offsets of shell vectors
-// [S, S + N)
-template <class C, int B, int S, int... I>
-__device__ __forceinline__ uint32_t count_i(const uint8_t* base, std::integer_sequence<int, I...>) {
-  return (0u + ... + (1u << base[NbrOff<C, B, S + I>::value]));
+// [S + LO, S + HI), summed as a balanced tree (independent adds)
+template <class C, int B, int S, int LO, int HI>
+__device__ __forceinline__ uint32_t count_i(const uint8_t* base) {
+  if constexpr (HI - LO == 1) {
+    return 1u << base[NbrOff<C, B, S + LO>::value];
+  } else {
+    constexpr int MID = (LO + HI) / 2;
+    return count_i<C, B, S, LO, MID>(base) + count_i<C, B, S, MID, HI>(base);
+  }
 }
 
-template <class C, int S, int... I>
-__device__ __forceinline__ uint32_t count_j_fcc(const uint8_t* const* cls_base,
-                                                std::integer_sequence<int, I...>) {
-  return (0u + ... + (1u << cls_base[Off0<C, S + I>::cls][Off0<C, S + I>::value]));
+template <class C, int S, int LO, int HI>
+__device__ __forceinline__ uint32_t count_j_fcc(const uint8_t* const* cls_base) {
+  if constexpr (HI - LO == 1) {
+    return 1u << cls_base[Off0<C, S + LO>::cls][Off0<C, S + LO>::value];
+  } else {
+    constexpr int MID = (LO + HI) / 2;
+    return count_j_fcc<C, S, LO, MID>(cls_base) + count_j_fcc<C, S, MID, HI>(cls_base);
+  }
 }
 
 template <class C, int B, int... Ms>
 __device__ __forceinline__ void count_all_i(const uint8_t* base, uint32_t* acc,
                                             std::integer_sequence<int, Ms...>) {
-  ((acc[Ms] = count_i<C, B, shell_start(C::KIND, Ms)>(
-        base, std::make_integer_sequence<int, shell_z(C::KIND, Ms)>{})),
-   ...);
+  ((acc[Ms] = count_i<C, B, shell_start(C::KIND, Ms), 0, shell_z(C::KIND, Ms)>(base)), ...);
 }
 
 template <class C, int... Ms>
 __device__ __forceinline__ void count_all_j_fcc(const uint8_t* const* cls_base, uint32_t* acc,
                                                 std::integer_sequence<int, Ms...>) {
-  ((acc[Ms] = count_j_fcc<C, shell_start(C::KIND, Ms)>(
-        cls_base, std::make_integer_sequence<int, shell_z(C::KIND, Ms)>{})),
-   ...);
+  ((acc[Ms] = count_j_fcc<C, shell_start(C::KIND, Ms), 0, shell_z(C::KIND, Ms)>(cls_base)), ...);
 }
 
-struct BlockGeo {
-  int lo[3];    // tile origin in shifted conventional coordinates (includes halo)
-  int ext[3];   // tile extent
-  int g0[3];    // global coordinate of tile origin
-  int off;      // byte offset of tile x = 0 inside a sub-row (8-byte alignment)
-  bool wrap_x;  // the tile's x range crosses the periodic seam
+// partner table entry e = b * Z1 + dir: (shared offset of the partner of a
+// basis-b anchor in first-shell direction dir) * 4 + the partner's basis
+template <class C, int E>
+struct PartnerEntry {
+  static constexpr int b = E / C::Z1, dir = E % C::Z1;
+  static constexpr ShellVec v = shell_vec(C::KIND, dir);
+  static constexpr int bj = basis_of_parity(C::KIND, (basis_comp(C::KIND, b, 0) + v.x) & 1,
+                                            (basis_comp(C::KIND, b, 1) + v.y) & 1,
+                                            (basis_comp(C::KIND, b, 2) + v.z) & 1);
+  static constexpr int value = nbr_offset<C>(b, v.x, v.y, v.z) * 4 + bj;
 };
 
-__device__ __forceinline__ int cell_bound(int c, int n, int m) {
-  return static_cast<int>((static_cast<long long>(c) * n) / m);
+template <class C, int... E>
+__device__ __forceinline__ void fill_partner_table(int* s_part, std::integer_sequence<int, E...>) {
+  ((s_part[E] = PartnerEntry<C, E>::value), ...);
 }
+
 
 __device__ __forceinline__ int wrapn(int v, int n) {
   v %= n;
@@ -173,93 +189,124 @@ __device__ __forceinline__ int wrapn(int v, int n) {
 }
 
 template <class C>
-__global__ void __launch_bounds__(C::NT) k_sweep_tiled(const Geom g, const PhaseArgs a,
+__global__ void __launch_bounds__(C::NT) k_sweep_tiled(const __grid_constant__ Geom g,
+                                                       const PhaseArgs a,
                                                        const __grid_constant__ Tables tab,
                                                        uint8_t* __restrict__ occ,
                                                        const uint32_t* __restrict__ dtab,
                                                        unsigned long long* __restrict__ stats) {
   extern __shared__ __align__(16) uint8_t smem[];
-  uint32_t* s_tab = reinterpret_cast<uint32_t*>(smem);                       // 1536 words
-  uint32_t* s_d = s_tab + kTabWords;                                         // DROWS * ROWW
-  int* s_part = reinterpret_cast<int*>(s_d + C::DROWS * C::ROWW);            // NB * Z1
+  uint32_t* s_tab = reinterpret_cast<uint32_t*>(smem);                      // 1536 words
+  uint8_t* s_d = smem + 4 * kTabWords;                                      // DBYTES
+  int* s_part = reinterpret_cast<int*>(s_d + C::DBYTES);                    // NB * Z1
   uint8_t* tile = smem + C::TILE_OFF;
 
   const int tid = threadIdx.x;
+  const int lane = tid & 31, warp = tid >> 5;
+  constexpr int NW = C::NT / 32;
   const int bit[3] = {a.colour & 1, (a.colour >> 1) & 1, (a.colour >> 2) & 1};
-  const int A[3] = {g.m[0] / 2, g.m[1] / 2, g.m[2] / 2};
   const int bidx[3] = {static_cast<int>(blockIdx.x), static_cast<int>(blockIdx.y),
                        static_cast<int>(blockIdx.z)};
-  const int Bsz[3] = {C::BX, C::BY, C::BZ};
+  constexpr int Bsz[3] = {C::BX, C::BY, C::BZ};
 
-  BlockGeo bg;
-  int a_first[3], a_last[3];
+  int lo[3], ext[3], g0[3], a_first[3], a_last[3];
 #pragma unroll
   for (int d = 0; d < 3; ++d) {
     a_first[d] = bidx[d] * Bsz[d];
-    a_last[d] = min(a_first[d] + Bsz[d], A[d]) - 1;
+    a_last[d] = min(a_first[d] + Bsz[d], g.m[d] / 2) - 1;
     const int c0 = 2 * a_first[d] + bit[d], c1 = 2 * a_last[d] + bit[d];
-    bg.lo[d] = cell_bound(c0, g.n[d], g.m[d]) - C::H;
-    bg.ext[d] = cell_bound(c1 + 1, g.n[d], g.m[d]) + C::H - bg.lo[d];
-    bg.g0[d] = wrapn(bg.lo[d] + a.shift[d], g.n[d]);
+    lo[d] = link_bound(g, d, c0) - C::H;
+    ext[d] = link_bound(g, d, c1 + 1) + C::H - lo[d];
+    int v = lo[d] + a.shift[d];
+    v += v < 0 ? g.n[d] : 0;
+    v -= v >= g.n[d] ? g.n[d] : 0;
+    g0[d] = v;
   }
-  bg.off = bg.g0[0] & 7;
-  bg.wrap_x = bg.g0[0] + bg.ext[0] > g.n[0];
+  const int off = g0[0] & 7;
+  const bool wrap_x = g0[0] + ext[0] > g.n[0];
 
   // ---- tables ------------------------------------------------------------
   for (int w = tid; w < kTabWords; w += C::NT) s_tab[w] = tab.w[w];
-  for (int w = tid; w < C::DROWS * C::ROWW; w += C::NT) s_d[w] = dtab[w];
-  for (int e = tid; e < C::NB * C::Z1; e += C::NT) {
-    const int b = e / C::Z1, dir = e % C::Z1;
-    const ShellVec v = shell_vec(C::KIND, dir);
-    const int off = nbr_offset<C>(b, v.x, v.y, v.z);
-    const int bj = basis_of_parity(C::KIND, (basis_comp(C::KIND, b, 0) + v.x) & 1,
-                                   (basis_comp(C::KIND, b, 1) + v.y) & 1,
-                                   (basis_comp(C::KIND, b, 2) + v.z) & 1);
-    s_part[e] = off * 4 + bj;
-  }
+  for (int w = tid; w < C::DBYTES / 4; w += C::NT)
+    reinterpret_cast<uint32_t*>(s_d)[w] = dtab[w];
+  if (tid == 0) fill_partner_table<C>(s_part, std::make_integer_sequence<int, C::NB * C::Z1>{});
 
   // ---- stage the tile ----------------------------------------------------
-  const int n_sub = bg.ext[1] * bg.ext[2] * C::G;  // device rows to copy
-  if (!bg.wrap_x) {
-    const int n8 = (bg.off + bg.ext[0] + 7) >> 3;
-    for (int item = tid; item < n_sub * n8; item += C::NT) {
-      const int chunk = item % n8;
-      const int sub = item / n8;
-      const int grp = sub % C::G;
-      const int ty = (sub / C::G) % bg.ext[1];
-      const int tz = sub / (C::G * bg.ext[1]);
-      const int gy = wrapn(bg.g0[1] + ty, g.n[1]);
-      const int gz = wrapn(bg.g0[2] + tz, g.n[2]);
-      const uint8_t* src = occ + dev_row(g, grp, gz, gy) + (bg.g0[0] - bg.off) + 8 * chunk;
-      const uint2 v = *reinterpret_cast<const uint2*>(src);
-      uint8_t* row = tile + tz * C::PS + ty * C::RS + 8 * chunk;
-      if constexpr (!C::PACK4) {
-        *reinterpret_cast<uint2*>(row + grp * C::XW) = v;
-      } else {
-        const uint2 lo = make_uint2((v.x & 0x0F0F0F0Fu) * C::W, (v.y & 0x0F0F0F0Fu) * C::W);
-        const uint2 hi = make_uint2(((v.x >> 4) & 0x0F0F0F0Fu) * C::W,
-                                    ((v.y >> 4) & 0x0F0F0F0Fu) * C::W);
-        *reinterpret_cast<uint2*>(row + (2 * grp) * C::XW) = lo;
-        *reinterpret_cast<uint2*>(row + (2 * grp + 1) * C::XW) = hi;
+  // sub-row index sub = (tz * ext_y + ty) * G + grp; tz = sub / (G ext_y) by a
+  // 16-bit reciprocal (exact: sub < 2^16 / 64, ext_y < 64)
+  const int n_sub = ext[1] * ext[2] * C::G;
+  const int ext_y = ext[1];
+  const uint32_t inv_ey = (65536u + ext_y - 1) / ext_y;
+  auto sub_row = [=](int sub, int* grp, int* ty, int* tz) {
+    *grp = sub % C::G;
+    const int t = sub / C::G;
+    *tz = static_cast<int>((static_cast<uint32_t>(t) * inv_ey) >> 16);
+    *ty = t - *tz * ext_y;
+  };
+  const int g0x = g0[0], g0y = g0[1], g0z = g0[2];
+  const int nx = g.n[0], ny = g.n[1], nz = g.n[2];
+  const size_t px = static_cast<size_t>(g.px);
+  auto grow = [=](int grp, int ty, int tz) -> size_t {
+    int gy = g0y + ty;
+    gy -= gy >= ny ? ny : 0;
+    int gz = g0z + tz;
+    gz -= gz >= nz ? nz : 0;
+    return ((static_cast<size_t>(grp) * nz + gz) * ny + gy) * px;
+  };
+  if (!wrap_x) {
+    const int n8 = (off + ext[0] + 7) >> 3;  // 8-byte chunks per sub-row (<= 32)
+    const int rpi = 32 / n8;                 // sub-rows per warp pass
+    const int my_r = lane / n8, my_c = lane - (lane / n8) * n8;
+    const uint8_t* src0 = occ + (g0[0] - off) + 8 * my_c;
+    if constexpr (!C::PACK4) {
+      // asynchronous 8-byte global -> shared copies, all in flight at once
+      const uint32_t sbase = static_cast<uint32_t>(__cvta_generic_to_shared(tile)) + 8 * my_c;
+      for (int base = warp * rpi; base < n_sub; base += NW * rpi) {
+        const int sub = base + my_r;
+        if (my_r < rpi && sub < n_sub) {
+          int grp, ty, tz;
+          sub_row(sub, &grp, &ty, &tz);
+          const uint32_t dst = sbase + tz * C::PS + ty * C::RS + grp * C::XW;
+          asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(dst),
+                       "l"(src0 + grow(grp, ty, tz))
+                       : "memory");
+        }
+      }
+      asm volatile("cp.async.wait_all;\n" ::: "memory");
+    } else {
+      for (int base = warp * rpi; base < n_sub; base += NW * rpi) {
+        const int sub = base + my_r;
+        if (my_r < rpi && sub < n_sub) {
+          int grp, ty, tz;
+          sub_row(sub, &grp, &ty, &tz);
+          const uint2 v = *reinterpret_cast<const uint2*>(src0 + grow(grp, ty, tz));
+          uint8_t* row = tile + tz * C::PS + ty * C::RS + 8 * my_c;
+          const uint2 lo4 = make_uint2((v.x & 0x0F0F0F0Fu) * C::W, (v.y & 0x0F0F0F0Fu) * C::W);
+          const uint2 hi4 = make_uint2(((v.x >> 4) & 0x0F0F0F0Fu) * C::W,
+                                       ((v.y >> 4) & 0x0F0F0F0Fu) * C::W);
+          *reinterpret_cast<uint2*>(row + (2 * grp) * C::XW) = lo4;
+          *reinterpret_cast<uint2*>(row + (2 * grp + 1) * C::XW) = hi4;
+        }
       }
     }
   } else {
-    for (int item = tid; item < n_sub * bg.ext[0]; item += C::NT) {
-      const int tx = item % bg.ext[0];
-      const int sub = item / bg.ext[0];
-      const int grp = sub % C::G;
-      const int ty = (sub / C::G) % bg.ext[1];
-      const int tz = sub / (C::G * bg.ext[1]);
-      const int gx = wrapn(bg.g0[0] + tx, g.n[0]);
-      const int gy = wrapn(bg.g0[1] + ty, g.n[1]);
-      const int gz = wrapn(bg.g0[2] + tz, g.n[2]);
-      const uint8_t v = occ[dev_row(g, grp, gz, gy) + gx];
-      uint8_t* row = tile + tz * C::PS + ty * C::RS + bg.off + tx;
-      if constexpr (!C::PACK4) {
-        row[grp * C::XW] = v;
-      } else {
-        row[(2 * grp) * C::XW] = static_cast<uint8_t>((v & 15) * C::W);
-        row[(2 * grp + 1) * C::XW] = static_cast<uint8_t>((v >> 4) * C::W);
+    // the tile's x range crosses the periodic seam: byte copies, one warp per
+    // sub-row
+    for (int sub = warp; sub < n_sub; sub += NW) {
+      int grp, ty, tz;
+      sub_row(sub, &grp, &ty, &tz);
+      const uint8_t* src = occ + grow(grp, ty, tz);
+      uint8_t* row = tile + tz * C::PS + ty * C::RS + off;
+      for (int tx = lane; tx < ext[0]; tx += 32) {
+        int gx = g0[0] + tx;
+        gx -= gx >= g.n[0] ? g.n[0] : 0;
+        const uint8_t v = src[gx];
+        if constexpr (!C::PACK4) {
+          row[grp * C::XW + tx] = v;
+        } else {
+          row[(2 * grp) * C::XW + tx] = static_cast<uint8_t>((v & 15) * C::W);
+          row[(2 * grp + 1) * C::XW + tx] = static_cast<uint8_t>((v >> 4) * C::W);
+        }
       }
     }
   }
@@ -268,42 +315,36 @@ __global__ void __launch_bounds__(C::NT) k_sweep_tiled(const Geom g, const Phase
   // ---- trials ------------------------------------------------------------
   uint32_t n_att = 0, n_unl = 0, n_acc = 0;
   int64_t sum_de = 0;
-  const int lane_a[3] = {tid % C::BX, (tid / C::BX) % C::BY, tid / (C::BX * C::BY)};
-  const int ac[3] = {a_first[0] + lane_a[0], a_first[1] + lane_a[1], a_first[2] + lane_a[2]};
+  const int la[3] = {tid % C::BX, (tid / C::BX) % C::BY, tid / (C::BX * C::BY)};
+  const int ac[3] = {a_first[0] + la[0], a_first[1] + la[1], a_first[2] + la[2]};
   if (ac[0] <= a_last[0] && ac[1] <= a_last[1] && ac[2] <= a_last[2]) {
     int o[3], l[3], c[3];
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
       c[d] = 2 * ac[d] + bit[d];
-      const int b0 = cell_bound(c[d], g.n[d], g.m[d]);
-      o[d] = b0 - bg.lo[d];
-      l[d] = cell_bound(c[d] + 1, g.n[d], g.m[d]) - b0;
+      const int b0 = link_bound(g, d, c[d]);
+      o[d] = b0 - lo[d];
+      l[d] = link_bound(g, d, c[d] + 1) - b0;
     }
     const uint32_t cid = (static_cast<uint32_t>(c[2]) * g.m[1] + c[1]) * g.m[0] + c[0];
     n_att = static_cast<uint32_t>(l[0] * l[1] * l[2] * C::NB);
 
-    // global address of a tile byte offset (it includes bg.off; for storing
-    // accepted swaps)
+    // store an accepted site to HBM; toff is its tile offset (includes off)
     auto store = [&](int toff, uint32_t code) {
       const int tz = toff / C::PS;
       const int r1 = toff - tz * C::PS;
       const int ty = r1 / C::RS;
       const int r2 = r1 - ty * C::RS;
       const int b = r2 / C::XW;
-      const int tx = r2 - b * C::XW - bg.off;
-      int gx = bg.g0[0] + tx;
-      gx -= gx >= g.n[0] ? g.n[0] : 0;
-      int gy = bg.g0[1] + ty;
-      gy -= gy >= g.n[1] ? g.n[1] : 0;
-      int gz = bg.g0[2] + tz;
-      gz -= gz >= g.n[2] ? g.n[2] : 0;
+      int gx = g0x + (r2 - b * C::XW - off);
+      gx -= gx >= nx ? nx : 0;
       if constexpr (!C::PACK4) {
-        occ[dev_row(g, b, gz, gy) + gx] = static_cast<uint8_t>(code);
+        occ[grow(b, ty, tz) + gx] = static_cast<uint8_t>(code);
       } else {
-        uint8_t* p = occ + dev_row(g, b >> 1, gz, gy) + gx;
+        uint8_t* q = occ + grow(b >> 1, ty, tz) + gx;
         const uint32_t sig = (code * (C::W == 6 ? 43u : 52u)) >> 8;
         const uint32_t sh = (b & 1) * 4u;
-        *p = static_cast<uint8_t>((*p & ~(15u << sh)) | (sig << sh));
+        *q = static_cast<uint8_t>((*q & ~(15u << sh)) | (sig << sh));
       }
     };
 
@@ -330,23 +371,32 @@ __global__ void __launch_bounds__(C::NT) k_sweep_tiled(const Geom g, const Phase
       }
       if (p == q) return;
       ++n_unl;
-      const uint32_t* row = s_d + (p * C::KMAX + q) * C::ROWW;
-      int64_t de = -static_cast<int64_t>((static_cast<uint64_t>(row[C::ROWW - 1]) << 32) |
-                                         row[C::ROWW - 2]);
+      const uint8_t* row = s_d + (p * C::KMAX + q) * C::RSTEP;
+      constexpr int ND = C::M * (C::KMAX - 1);
+      int32_t dr[(ND + 3) / 4 * 4];
+#pragma unroll
+      for (int v = 0; v < (ND + 3) / 4; ++v) {
+        const int4 d4 = reinterpret_cast<const int4*>(row)[v];
+        dr[4 * v] = d4.x;
+        dr[4 * v + 1] = d4.y;
+        dr[4 * v + 2] = d4.z;
+        dr[4 * v + 3] = d4.w;
+      }
+      long long de = -*reinterpret_cast<const long long*>(row + C::DOFF_C);
 #pragma unroll
       for (int m = 0; m < C::M; ++m) {
         if constexpr (C::KMAX <= 5) {
-          const uint32_t F = 0x20820820u + acc_i[m] - acc_j[m];  // bias 32 in each 6-bit field
+          const uint32_t F = 0x20820820u + acc_i[m] - acc_j[m];  // bias 32 per 6-bit field
 #pragma unroll
           for (int s = 1; s < C::KMAX; ++s)
-            de += static_cast<int64_t>((F >> (6 * s)) & 63u) *
-                  static_cast<int32_t>(row[m * (C::KMAX - 1) + s - 1]);
+            de += static_cast<long long>(static_cast<int>((F >> (6 * s)) & 63u)) *
+                  static_cast<long long>(dr[m * (C::KMAX - 1) + s - 1]);
         } else {
 #pragma unroll
           for (int s = 1; s < C::KMAX; ++s)
-            de += static_cast<int64_t>(static_cast<int>((acc_i[m] >> (5 * s)) & 31u) -
-                                       static_cast<int>((acc_j[m] >> (5 * s)) & 31u)) *
-                  static_cast<int32_t>(row[m * (C::KMAX - 1) + s - 1]);
+            de += static_cast<long long>(static_cast<int>((acc_i[m] >> (5 * s)) & 31u) -
+                                         static_cast<int>((acc_j[m] >> (5 * s)) & 31u)) *
+                  static_cast<long long>(dr[m * (C::KMAX - 1) + s - 1]);
         }
       }
       bool ok;
@@ -374,15 +424,16 @@ __global__ void __launch_bounds__(C::NT) k_sweep_tiled(const Geom g, const Phase
 
     for (int zr = 0; zr < l[2]; ++zr)
       for (int yr = 0; yr < l[1]; ++yr) {
-        const int rb = bg.off + (o[2] + zr) * C::PS + (o[1] + yr) * C::RS + o[0];
+        const int rb = off + (o[2] + zr) * C::PS + (o[1] + yr) * C::RS + o[0];
+        const uint32_t cc0 = static_cast<uint32_t>((zr * l[1] + yr) * l[0]);
         for (int xr = 0; xr < l[0]; ++xr) {
-          const uint32_t cc = static_cast<uint32_t>((zr * l[1] + yr) * l[0] + xr);
+          const uint32_t cc = cc0 + xr;
           const int ai = rb + xr;
-          const U4 w0 = philox4x32_10(cc * (C::NB / 2), cid, a.t, 0u, g.seed_lo, g.seed_hi);
+          const U4 w0 = philox4x32_10_rk(cc * (C::NB / 2), cid, a.t, 0u, g.rk);
           attempt(std::integral_constant<int, 0>{}, ai, w0.x, w0.y);
           attempt(std::integral_constant<int, 1>{}, ai + C::XW, w0.z, w0.w);
           if constexpr (C::NB == 4) {
-            const U4 w1 = philox4x32_10(cc * 2 + 1, cid, a.t, 0u, g.seed_lo, g.seed_hi);
+            const U4 w1 = philox4x32_10_rk(cc * 2 + 1, cid, a.t, 0u, g.rk);
             attempt(std::integral_constant<int, 2>{}, ai + 2 * C::XW, w1.x, w1.y);
             attempt(std::integral_constant<int, 3>{}, ai + 3 * C::XW, w1.z, w1.w);
           }

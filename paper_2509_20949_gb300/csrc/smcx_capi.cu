@@ -92,7 +92,7 @@ struct WorkLayout {
   size_t total;
 };
 
-constexpr size_t kTiledTableWords = 6 * 5 * 6 * 22;  // largest DROWS * ROWW (K = 6, M = 4)
+constexpr size_t kTiledTableWords = 6 * 6 * 160 / 4;  // largest table: K = 6, M = 4
 
 WorkLayout work_layout(const smcx_lattice_desc* d) {
   const size_t K = d->n_species;
@@ -218,6 +218,20 @@ struct smcx_lattice {
     g.W = desc.pack_bits == 4 ? 1 : code_width(g.K);
     g.seed_lo = static_cast<uint32_t>(desc.seed);
     g.seed_hi = static_cast<uint32_t>(desc.seed >> 32);
+    for (int c = 0; c < 3; ++c) {
+      const uint32_t md = static_cast<uint32_t>(m[c]);
+      g.bq[c] = desc.n[c] / md;
+      g.br[c] = desc.n[c] % md;
+      g.bmag[c] = md == 1 ? 0xFFFFFFFFu
+                          : (md <= 1600 ? static_cast<uint32_t>(((1ull << 32) + md - 1) / md) : 0u);
+    }
+    uint32_t k0 = g.seed_lo, k1 = g.seed_hi;
+    for (int r = 0; r < 10; ++r) {
+      g.rk[r][0] = k0;
+      g.rk[r][1] = k1;
+      k0 += 0x9E3779B9u;
+      k1 += 0xBB67AE85u;
+    }
     return g;
   }
 };
@@ -405,8 +419,6 @@ smcx_status launch_colour(smcx_lattice* lat, int colour, const PhaseArgs& base, 
   if (kern == 2) {
     TiledEpi te;
     te.kmax = lat->tiled_kmax;
-    te.row_words = tiled_row_words(g.M, te.kmax);
-    te.n_rows = te.kmax * code_width(g.K) * te.kmax;
     te.d_table = lat->dtab();
     SMCX_CUDA(lat, launch_sweep_tiled(g, a, tab, lat->d_occ, te, lat->stats(), tiled_shape_for(lat),
                                       lat->stream));
@@ -418,9 +430,9 @@ smcx_status launch_colour(smcx_lattice* lat, int colour, const PhaseArgs& base, 
   return SMCX_OK;
 }
 
-// Difference rows of the tiled kernel, one per pair of species codes
-// (code = sigma * W, row = code_p * KMAX + code_q): D'_{m,s} = D_{m,s} - D_{m,0}
-// for s = 1..K-1 with D_{m,s} = V_m(q,s) - V_m(p,s), then the int64 constant
+// Difference rows of the tiled kernel, one per species pair (p, q) at byte
+// (p * KMAX + q) * row_bytes: D'_{m,s} = D_{m,s} - D_{m,0} (int32) for
+// s = 1..K-1 with D_{m,s} = V_m(q,s) - V_m(p,s), then the int64 constant
 // C = [32 sum_{m,s} D'_{m,s} when K <= 5] + D_{1,q} - D_{1,p}.  Returns false
 // when a D' does not fit int32.
 bool build_tiled_table(smcx_lattice* lat, std::vector<uint32_t>* out) {
@@ -428,29 +440,31 @@ bool build_tiled_table(smcx_lattice* lat, std::vector<uint32_t>* out) {
   const int M = static_cast<int>(lat->M);
   if (K > 6 || M < 2) return false;
   const int kmax = K <= 5 ? 5 : 6;
-  const int W = code_width(K);
-  const int roww = tiled_row_words(M, kmax);
-  out->assign(static_cast<size_t>(kmax) * W * kmax * roww, 0u);
+  const int rowb = tiled_row_bytes(M, kmax);
+  const int doff = tiled_doff_c(M, kmax);
+  std::vector<uint8_t> bytes(static_cast<size_t>(kmax) * kmax * rowb, 0);
   auto V = [&](int m, int a, int b) { return lat->V[(static_cast<size_t>(m) * K + a) * K + b]; };
   for (int p = 0; p < K; ++p)
     for (int q = 0; q < K; ++q) {
-      uint32_t* row = out->data() + (static_cast<size_t>(p * W) * kmax + q * W) * roww;
+      uint8_t* row = bytes.data() + static_cast<size_t>(p * kmax + q) * rowb;
       __int128 C = 0;
       for (int m = 0; m < M; ++m) {
         const int64_t d0 = V(m, q, 0) - V(m, p, 0);
         for (int s = 1; s < K; ++s) {
           const int64_t dp = (V(m, q, s) - V(m, p, s)) - d0;
           if (dp > INT32_MAX || dp < INT32_MIN) return false;
-          row[m * (kmax - 1) + s - 1] = static_cast<uint32_t>(static_cast<int32_t>(dp));
+          const int32_t v32 = static_cast<int32_t>(dp);
+          std::memcpy(row + 4 * (m * (kmax - 1) + s - 1), &v32, 4);
           if (kmax == 5) C += static_cast<__int128>(32) * dp;
         }
       }
       C += (V(0, q, q) - V(0, p, q)) - (V(0, q, p) - V(0, p, p));
       if (C > INT64_MAX || C < INT64_MIN) return false;
-      const uint64_t c64 = static_cast<uint64_t>(static_cast<int64_t>(C));
-      row[roww - 2] = static_cast<uint32_t>(c64);
-      row[roww - 1] = static_cast<uint32_t>(c64 >> 32);
+      const int64_t c64 = static_cast<int64_t>(C);
+      std::memcpy(row + doff, &c64, 8);
     }
+  out->assign(bytes.size() / 4, 0u);
+  std::memcpy(out->data(), bytes.data(), bytes.size());
   lat->tiled_kmax = kmax;
   return true;
 }

@@ -150,7 +150,38 @@ struct Geom {
   int px;         // device row pitch in bytes (multiple of 16)
   int W;          // code multiplier of 8-bit storage
   uint32_t seed_lo, seed_hi;
+  uint32_t rk[10][2];  // Philox round keys of the seed (host-precomputed)
+  // link-cell bounds floor(c n_d / m_d) = c q_d + floor(c r_d / m_d) with
+  // n_d = q_d m_d + r_d; the last term is umulhi(c r_d, bmag_d) with
+  // bmag_d = ceil(2^32 / m_d), exact while c r_d < m_d^2 < 2^32 / m_d
+  // (m_d <= 1600; bmag_d = 0 selects a 64-bit division)
+  uint32_t bq[3], br[3], bmag[3];
 };
+
+__host__ __device__ __forceinline__ int link_bound(const Geom& g, int d, int c) {
+  if (g.bmag[d])
+    return static_cast<int>(static_cast<uint32_t>(c) * g.bq[d] +
+                            mulhi32(static_cast<uint32_t>(c) * g.br[d], g.bmag[d]));
+  return static_cast<int>((static_cast<long long>(c) * g.n[d]) / g.m[d]);
+}
+
+// Philox4x32-10 with the ten round keys precomputed (same generator as
+// philox4x32_10; the key schedule is a pure function of the seed).
+__host__ __device__ __forceinline__ U4 philox4x32_10_rk(uint32_t c0, uint32_t c1, uint32_t c2,
+                                                        uint32_t c3, const uint32_t (*rk)[2]) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    const uint32_t a_lo = 0xD2511F53u * c0, a_hi = mulhi32(0xD2511F53u, c0);
+    const uint32_t b_lo = 0xCD9E8D57u * c2, b_hi = mulhi32(0xCD9E8D57u, c2);
+    const uint32_t n0 = b_hi ^ c1 ^ rk[r][0];
+    const uint32_t n2 = a_hi ^ c3 ^ rk[r][1];
+    c0 = n0;
+    c1 = b_lo;
+    c2 = n2;
+    c3 = a_lo;
+  }
+  return U4{c0, c1, c2, c3};
+}
 
 __host__ __device__ inline int code_width(int K) { return K <= 5 ? 6 : (K == 6 ? 5 : 1); }
 

@@ -1,19 +1,35 @@
-// tiled_dispatch.cu -- selection of the tiled sweep instantiation.
+// tiled_dispatch.cu -- selection of the tiled sweep instantiation: the
+// exact-extent (uniform edge) tiles first, the ragged ones otherwise.
 #include "kernels.h"
 
 namespace smcx {
 namespace tiled {
-cudaError_t dispatch_bcc(int shape, const Geom& g, const PhaseArgs& a, const Tables& tab,
-                         uint8_t* occ, const TiledEpi& epi, unsigned long long* stats,
-                         cudaStream_t st, bool check_only, bool* ok);
-cudaError_t dispatch_fcc(int shape, const Geom& g, const PhaseArgs& a, const Tables& tab,
-                         uint8_t* occ, const TiledEpi& epi, unsigned long long* stats,
-                         cudaStream_t st, bool check_only, bool* ok);
-void bcc_shape_cells(int shape, int cells[3]);
-void fcc_shape_cells(int shape, int cells[3]);
+#define SMCX_DECL(NAME)                                                                      \
+  cudaError_t NAME(int shape, const Geom& g, const PhaseArgs& a, const Tables& tab,         \
+                   uint8_t* occ, const TiledEpi& epi, unsigned long long* stats,             \
+                   cudaStream_t st, bool check_only, bool* ok);
+SMCX_DECL(dispatch_bcc_uniform)
+SMCX_DECL(dispatch_bcc_ragged)
+SMCX_DECL(dispatch_fcc_uniform)
+SMCX_DECL(dispatch_fcc_ragged)
+#undef SMCX_DECL
+
+static cudaError_t dispatch(int shape, const Geom& g, const PhaseArgs& a, const Tables& tab,
+                            uint8_t* occ, const TiledEpi& epi, unsigned long long* stats,
+                            cudaStream_t st, bool check_only, bool* ok) {
+  cudaError_t e;
+  if (g.kind == 0) {
+    e = dispatch_bcc_uniform(shape, g, a, tab, occ, epi, stats, st, check_only, ok);
+    if (*ok) return e;
+    return dispatch_bcc_ragged(shape, g, a, tab, occ, epi, stats, st, check_only, ok);
+  }
+  e = dispatch_fcc_uniform(shape, g, a, tab, occ, epi, stats, st, check_only, ok);
+  if (*ok) return e;
+  return dispatch_fcc_ragged(shape, g, a, tab, occ, epi, stats, st, check_only, ok);
+}
 }  // namespace tiled
 
-int tiled_row_words(int M, int kmax) { return (M * (kmax - 1) + 2 + 1) / 2 * 2; }
+static const int kShapeCells[2][2][3] = {{{16, 2, 8}, {16, 2, 4}}, {{16, 2, 4}, {16, 2, 2}}};
 
 int tiled_shape_count(int kind) {
   (void)kind;
@@ -21,21 +37,15 @@ int tiled_shape_count(int kind) {
 }
 
 void tiled_shape_cells(int kind, int shape, int cells[3]) {
-  if (kind == 0)
-    tiled::bcc_shape_cells(shape, cells);
-  else
-    tiled::fcc_shape_cells(shape, cells);
+  for (int d = 0; d < 3; ++d) cells[d] = kShapeCells[kind][shape][d];
 }
 
 bool tiled_supported(const Geom& g, int shape) {
   bool ok = false;
-  Tables* none = nullptr;
+  const Tables* none = nullptr;
   PhaseArgs a{};
   TiledEpi e{};
-  if (g.kind == 0)
-    tiled::dispatch_bcc(shape, g, a, *none, nullptr, e, nullptr, nullptr, true, &ok);
-  else
-    tiled::dispatch_fcc(shape, g, a, *none, nullptr, e, nullptr, nullptr, true, &ok);
+  tiled::dispatch(shape, g, a, *none, nullptr, e, nullptr, nullptr, true, &ok);
   return ok;
 }
 
@@ -43,9 +53,7 @@ cudaError_t launch_sweep_tiled(const Geom& g, const PhaseArgs& a, const Tables& 
                                const TiledEpi& epi, unsigned long long* stats, int shape,
                                cudaStream_t st) {
   bool ok = false;
-  const cudaError_t e =
-      g.kind == 0 ? tiled::dispatch_bcc(shape, g, a, tab, occ, epi, stats, st, false, &ok)
-                  : tiled::dispatch_fcc(shape, g, a, tab, occ, epi, stats, st, false, &ok);
+  const cudaError_t e = tiled::dispatch(shape, g, a, tab, occ, epi, stats, st, false, &ok);
   if (!ok) return cudaErrorNotSupported;
   return e;
 }

@@ -55,8 +55,10 @@ def test_tiled_matches_oracle(orc, kind, n, K, M):
 @pytest.mark.parametrize("pack", [8, 4])
 @pytest.mark.parametrize("shape", [0, 1])
 def test_tiled_shapes_and_packing(orc, pack, shape):
-    case = make_case(0, (69, 12, 20), 5, 3, seed=2, sigma=0.02)
+    case = make_case(0, (69, 12, 36), 5, 3, seed=2, sigma=0.02)
     _compare_sweeps(orc, case, 2, 1100.0, pack_bits=pack, shape=shape)
+    case = make_case(0, (68, 12, 36), 6, 2, seed=4, sigma=0.02)  # uniform edges
+    _compare_sweeps(orc, case, 2, 900.0, pack_bits=pack, shape=shape)
     case = make_case(1, (68, 13, 20), 4, 4, seed=5, sigma=0.02)
     _compare_sweeps(orc, case, 2, 700.0, pack_bits=pack, shape=shape)
 
