@@ -7,7 +7,8 @@
 // cells plus a two-conventional-cell halo (the local interaction zone of
 // every trial, Sec. 2.2) from HBM into shared memory with 8-byte vector
 // loads, runs the trials on the shared tile and stores every accepted swap
-// straight back to HBM.
+// straight back to HBM (global addresses follow the loop counters; tiles that
+// cross a periodic seam decompose the shared offset instead).
 //
 // Energy change of a trial (EPI model, Sec. 3): with p = sigma_i, q = sigma_j,
 //   dE = sum_m sum_s dx_{m,s} (V_m(q,s) - V_m(p,s)) - (V_1(p,p)+V_1(q,q)-2V_1(p,q)),
@@ -79,6 +80,9 @@ struct Cfg {
   static constexpr int PS = RS * EXT_Y;
   static constexpr int W = KMAX <= 5 ? 6 : 5;
   static constexpr int NT = BX * BY * BZ;
+  // resident blocks per SM the register budget must allow (shared memory
+  // admits about as many)
+  static constexpr int MINB = NT >= 256 ? 3 : (NT >= 128 ? 4 : 6);
   static constexpr int Z1 = shell_z(KIND, 0);
   static constexpr int NV = shell_start(KIND, M);
   // difference rows: int32 D'[m][s-1] then the int64 constant C at DOFF_C;
@@ -89,8 +93,8 @@ struct Cfg {
   static constexpr int RSTEP = ROWB / W;
   static constexpr int DBYTES = KMAX * KMAX * ROWB;
   static constexpr int G = PACK4 ? NB / 2 : NB;                   // device row groups
-  static constexpr int TILE_OFF =
-      round_up(4 * kTabWords + DBYTES + 4 * NB * Z1, 16);         // shared bytes before the tile
+  static constexpr int GPART_OFF = round_up(4 * kTabWords + DBYTES + 4 * NB * Z1, 8);
+  static constexpr int TILE_OFF = round_up(GPART_OFF + 8 * NB * Z1, 16);  // bytes before the tile
   static_assert(RS % 32 == BANK % 32, "bank padding");
   static_assert(RS % 8 == 0 && XW % 8 == 0, "8-byte alignment of the tile rows");
 };
@@ -182,14 +186,43 @@ __device__ __forceinline__ void fill_partner_table(int* s_part, std::integer_seq
   ((s_part[E] = PartnerEntry<C, E>::value), ...);
 }
 
+// conventional-cell shift (dx, dy, dz) and basis of the partner of a basis-b
+// anchor in first-shell direction dir
+template <class C, int... E>
+__device__ __forceinline__ void partner_shift_impl(int e, int* dx, int* dy, int* dz, int* bj,
+                                                   std::integer_sequence<int, E...>) {
+  ((e == E ? (*dx = floordiv2(basis_comp(C::KIND, PartnerEntry<C, E>::b, 0) + PartnerEntry<C, E>::v.x),
+              *dy = floordiv2(basis_comp(C::KIND, PartnerEntry<C, E>::b, 1) + PartnerEntry<C, E>::v.y),
+              *dz = floordiv2(basis_comp(C::KIND, PartnerEntry<C, E>::b, 2) + PartnerEntry<C, E>::v.z),
+              *bj = PartnerEntry<C, E>::bj, 0)
+           : 0),
+   ...);
+}
+
+template <class C>
+__device__ __forceinline__ void partner_shift(int b, int dir, int* dx, int* dy, int* dz, int* bj) {
+  partner_shift_impl<C>(b * C::Z1 + dir, dx, dy, dz, bj,
+                        std::make_integer_sequence<int, C::NB * C::Z1>{});
+}
+
 
 __device__ __forceinline__ int wrapn(int v, int n) {
   v %= n;
   return v < 0 ? v + n : v;
 }
 
+// sigma of each byte of a word of codes sigma * W (sigma <= 5): per 16-bit lane
+// (code * ceil(256 / W)) >> 8, exact for codes <= 30
+template <int W>
+__device__ __forceinline__ uint32_t codes_to_sigma(uint32_t w) {
+  constexpr uint32_t mul = W == 6 ? 43u : 52u;
+  const uint32_t even = (((w & 0x00FF00FFu) * mul) >> 8) & 0x00FF00FFu;
+  const uint32_t odd = ((((w >> 8) & 0x00FF00FFu) * mul) >> 8) & 0x00FF00FFu;
+  return even | (odd << 8);
+}
+
 template <class C>
-__global__ void __launch_bounds__(C::NT) k_sweep_tiled(const __grid_constant__ Geom g,
+__global__ void __launch_bounds__(C::NT, C::MINB) k_sweep_tiled(const __grid_constant__ Geom g,
                                                        const PhaseArgs a,
                                                        const __grid_constant__ Tables tab,
                                                        uint8_t* __restrict__ occ,
@@ -199,6 +232,7 @@ __global__ void __launch_bounds__(C::NT) k_sweep_tiled(const __grid_constant__ G
   uint32_t* s_tab = reinterpret_cast<uint32_t*>(smem);                      // 1536 words
   uint8_t* s_d = smem + 4 * kTabWords;                                      // DBYTES
   int* s_part = reinterpret_cast<int*>(s_d + C::DBYTES);                    // NB * Z1
+  long long* s_gpart = reinterpret_cast<long long*>(smem + C::GPART_OFF);    // NB * Z1
   uint8_t* tile = smem + C::TILE_OFF;
 
   const int tid = threadIdx.x;
@@ -224,12 +258,23 @@ __global__ void __launch_bounds__(C::NT) k_sweep_tiled(const __grid_constant__ G
   }
   const int off = g0[0] & 7;
   const bool wrap_x = g0[0] + ext[0] > g.n[0];
+  const bool wrap_any = wrap_x || g0[1] + ext[1] > g.n[1] || g0[2] + ext[2] > g.n[2];
 
   // ---- tables ------------------------------------------------------------
   for (int w = tid; w < kTabWords; w += C::NT) s_tab[w] = tab.w[w];
   for (int w = tid; w < C::DBYTES / 4; w += C::NT)
     reinterpret_cast<uint32_t*>(s_d)[w] = dtab[w];
   if (tid == 0) fill_partner_table<C>(s_part, std::make_integer_sequence<int, C::NB * C::Z1>{});
+  // device-storage offset of the partner (no periodic wrap): conventional
+  // cell offsets along x, y, z and the change of basis (8-bit storage)
+  const long long zstr = static_cast<long long>(g.n[1]) * g.px;          // z step
+  const long long gstr = zstr * g.n[2];                                  // basis-row step
+  if (tid < C::NB * C::Z1) {
+    const int b = tid / C::Z1, dir = tid % C::Z1;
+    int dx = 0, dy = 0, dz = 0, bj = 0;
+    partner_shift<C>(b, dir, &dx, &dy, &dz, &bj);
+    s_gpart[tid] = dx + dy * static_cast<long long>(g.px) + dz * zstr + (bj - b) * gstr;
+  }
 
   // ---- stage the tile ----------------------------------------------------
   // sub-row index sub = (tz * ext_y + ty) * G + grp; tz = sub / (G ext_y) by a
@@ -329,8 +374,9 @@ __global__ void __launch_bounds__(C::NT) k_sweep_tiled(const __grid_constant__ G
     const uint32_t cid = (static_cast<uint32_t>(c[2]) * g.m[1] + c[1]) * g.m[0] + c[0];
     n_att = static_cast<uint32_t>(l[0] * l[1] * l[2] * C::NB);
 
-    // store an accepted site to HBM; toff is its tile offset (includes off)
-    auto store = [&](int toff, uint32_t code) {
+    // store of an accepted site by decomposing its shared offset toff
+    // (includes off): tiles that cross a periodic seam, and packed storage
+    auto store_slow = [&](int toff, uint32_t code) {
       const int tz = toff / C::PS;
       const int r1 = toff - tz * C::PS;
       const int ty = r1 / C::RS;
@@ -347,8 +393,12 @@ __global__ void __launch_bounds__(C::NT) k_sweep_tiled(const __grid_constant__ G
         *q = static_cast<uint8_t>((*q & ~(15u << sh)) | (sig << sh));
       }
     };
+    const bool fast_store = !C::PACK4 && !wrap_any;
+    // device address of this cell's first site (8-bit storage, no wrap)
+    uint8_t* const gcell = occ + (static_cast<long long>(g0z + o[2]) * ny + (g0y + o[1])) * px +
+                           (g0x + o[0]);
 
-    auto attempt = [&](auto bconst, int ai, uint32_t wa, uint32_t wb) {
+    auto attempt = [&](auto bconst, int ai, uint8_t* gi, uint32_t wa, uint32_t wb) {
       constexpr int B = decltype(bconst)::value;
       const uint32_t dir = __umulhi(wa, static_cast<uint32_t>(C::Z1));
       const int pt = s_part[B * C::Z1 + dir];
@@ -369,8 +419,8 @@ __global__ void __launch_bounds__(C::NT) k_sweep_tiled(const __grid_constant__ G
         }
         count_all_j_fcc<C>(cls_base, acc_j, std::make_integer_sequence<int, C::M>{});
       }
-      if (p == q) return;
-      ++n_unl;
+      const bool unlike = p != q;
+      n_unl += unlike;
       const uint8_t* row = s_d + (p * C::KMAX + q) * C::RSTEP;
       constexpr int ND = C::M * (C::KMAX - 1);
       int32_t dr[(ND + 3) / 4 * 4];
@@ -399,24 +449,24 @@ __global__ void __launch_bounds__(C::NT) k_sweep_tiled(const __grid_constant__ G
                   static_cast<long long>(dr[m * (C::KMAX - 1) + s - 1]);
         }
       }
-      bool ok;
-      if (de <= 0) {
-        ok = true;
-      } else if (a.mode == kModeZeroT) {
-        ok = false;
-      } else if (a.mode == kModeAcceptAll) {
-        ok = true;
-      } else {
-        const uint64_t idx = static_cast<uint64_t>(de) >> a.s;
-        ok = idx < (1ull << 27) &&
-             wb < compose_threshold(s_tab[idx & 511u], s_tab[512 + ((idx >> 9) & 511u)],
-                                    s_tab[1024 + (idx >> 18)]);
-      }
+      // Metropolis (Sec. 2.1, Eq. 3) without branches: the table lookups are
+      // clamped in range and only matter when dE > 0 in normal mode
+      const uint64_t idx = static_cast<uint64_t>(de) >> a.s;
+      const uint32_t i2 = idx >> 18 < 511u ? static_cast<uint32_t>(idx >> 18) : 511u;
+      const uint32_t thr = compose_threshold(s_tab[idx & 511u], s_tab[512 + ((idx >> 9) & 511u)],
+                                             s_tab[1024 + i2]);
+      const bool ok = unlike && (de <= 0 || a.mode == kModeAcceptAll ||
+                                 (a.mode == kModeNormal && idx < (1ull << 27) && wb < thr));
       if (ok) {
         tile[ai] = static_cast<uint8_t>(q);
         tile[aj] = static_cast<uint8_t>(p);
-        store(ai, q);
-        store(aj, p);
+        if (fast_store) {
+          gi[0] = static_cast<uint8_t>(q);
+          gi[s_gpart[B * C::Z1 + dir]] = static_cast<uint8_t>(p);
+        } else {
+          store_slow(ai, q);
+          store_slow(aj, p);
+        }
         ++n_acc;
         sum_de += de;
       }
@@ -425,17 +475,19 @@ __global__ void __launch_bounds__(C::NT) k_sweep_tiled(const __grid_constant__ G
     for (int zr = 0; zr < l[2]; ++zr)
       for (int yr = 0; yr < l[1]; ++yr) {
         const int rb = off + (o[2] + zr) * C::PS + (o[1] + yr) * C::RS + o[0];
+        uint8_t* const grb = gcell + zr * zstr + yr * px;
         const uint32_t cc0 = static_cast<uint32_t>((zr * l[1] + yr) * l[0]);
         for (int xr = 0; xr < l[0]; ++xr) {
           const uint32_t cc = cc0 + xr;
           const int ai = rb + xr;
+          uint8_t* const gi = grb + xr;
           const U4 w0 = philox4x32_10_rk(cc * (C::NB / 2), cid, a.t, 0u, g.rk);
-          attempt(std::integral_constant<int, 0>{}, ai, w0.x, w0.y);
-          attempt(std::integral_constant<int, 1>{}, ai + C::XW, w0.z, w0.w);
+          attempt(std::integral_constant<int, 0>{}, ai, gi, w0.x, w0.y);
+          attempt(std::integral_constant<int, 1>{}, ai + C::XW, gi + gstr, w0.z, w0.w);
           if constexpr (C::NB == 4) {
             const U4 w1 = philox4x32_10_rk(cc * 2 + 1, cid, a.t, 0u, g.rk);
-            attempt(std::integral_constant<int, 2>{}, ai + 2 * C::XW, w1.x, w1.y);
-            attempt(std::integral_constant<int, 3>{}, ai + 3 * C::XW, w1.z, w1.w);
+            attempt(std::integral_constant<int, 2>{}, ai + 2 * C::XW, gi + 2 * gstr, w1.x, w1.y);
+            attempt(std::integral_constant<int, 3>{}, ai + 3 * C::XW, gi + 3 * gstr, w1.z, w1.w);
           }
         }
       }
