@@ -6,8 +6,8 @@
 // over the whole shell are N_m = H_m + H_m^T (substitute i -> i - d), which
 // the host forms.  A persistent grid walks boxes of 64 x 8 x 8 conventional
 // cells; each box plus its halo (+2 cells in x, +-2 in y and z: half-shell
-// vectors never point to smaller x) is staged into shared memory with 8-byte
-// loads.  One thread per x column sums, for each site and shell, a one-hot
+// vectors never point to smaller x) is staged into shared memory with
+// asynchronous 8-byte copies, the next box prefetched while one is counted.  One thread per x column sums, for each site and shell, a one-hot
 // 64-bit word over the neighbour species (FW-bit fields), masked into the
 // row of the centre's species; the fields are warp-reduced and added to
 // shared counters once per box (twice for FCC with 10-bit fields).
@@ -82,75 +82,105 @@ __device__ __forceinline__ void all_shells(const uint8_t* base, unsigned long lo
    ...);
 }
 
+__device__ __forceinline__ int pwrap(int v, int n) {
+  if (v < 0) v += n;
+  if (v >= n) v -= n;
+  if (v < 0 || v >= n) v = ((v % n) + n) % n;  // lattices thinner than the halo
+  return v;
+}
+
 template <class C>
-__global__ void __launch_bounds__(C::NT) k_pair_count_tiled(const Geom g,
+__global__ void __launch_bounds__(C::NT) k_pair_count_tiled(const __grid_constant__ Geom g,
                                                             const uint8_t* __restrict__ occ,
                                                             unsigned long long* __restrict__ hcnt) {
   extern __shared__ __align__(16) uint8_t smem[];
   uint32_t* s_cnt = reinterpret_cast<uint32_t*>(smem);
-  uint8_t* tile = smem + round_up(4 * C::NCNT, 16);
-  const int tid = threadIdx.x;
+  uint8_t* tiles = smem + round_up(4 * C::NCNT, 16);  // two box buffers of C::TILE bytes
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  constexpr int NW = C::NT / 32;
   for (int i = tid; i < C::NCNT; i += C::NT) s_cnt[i] = 0;
 
-  const int nbx = (g.n[0] + C::BXC - 1) / C::BXC;
-  const int nby = (g.n[1] + C::BYC - 1) / C::BYC;
-  const int nbz = (g.n[2] + C::BZC - 1) / C::BZC;
+  const int nx = g.n[0], ny = g.n[1], nz = g.n[2];
+  const int nbx = (nx + C::BXC - 1) / C::BXC;
+  const int nby = (ny + C::BYC - 1) / C::BYC;
+  const int nbz = (nz + C::BZC - 1) / C::BZC;
   const int n_boxes = nbx * nby * nbz;
   const int xl = tid % C::BXC;  // this thread's x column inside the box
   const int rg = tid / C::BXC;  // 0 or 1: row parity
+  const size_t px = static_cast<size_t>(g.px);
 
-  for (int box = blockIdx.x; box < n_boxes; box += gridDim.x) {
+  // stage box `box` into buffer `buf`: x in [x0, x0 + ex), y in [y0 - 2, y0 + 10),
+  // z in [z0 - 2, z0 + 10); 8-bit storage without an x seam goes through
+  // cp.async (completes later), everything else is copied synchronously
+  auto stage = [&](int box, uint8_t* tile) {
     const int x0 = (box % nbx) * C::BXC;
     const int y0 = ((box / nbx) % nby) * C::BYC;
     const int z0 = (box / (nbx * nby)) * C::BZC;
-    const int ex = min(C::TX, g.n[0] - x0 + C::HX);  // staged x extent (<= n_x cells + halo)
-    __syncthreads();                                // previous box finished with the tile
-    // ---- stage: x in [x0, x0 + ex), y in [y0 - 2, y0 + 10), z in [z0 - 2, z0 + 10)
-    const bool wrap = x0 + ex > g.n[0];
-    const int n_sub = C::TY * C::TZ * C::G;
-    if (!wrap) {
+    const int ex = min(C::TX, nx - x0 + C::HX);
+    constexpr int n_sub = C::TY * C::TZ * C::G;
+    if (x0 + ex <= nx) {
       const int n8 = (ex + 7) >> 3;
-      for (int item = tid; item < n_sub * n8; item += C::NT) {
-        const int chunk = item % n8;
-        const int sub = item / n8;
-        const int grp = sub % C::G;
-        const int ty = (sub / C::G) % C::TY;
-        const int tz = sub / (C::G * C::TY);
-        const int gy = tiled::wrapn(y0 - C::HYZ + ty, g.n[1]);
-        const int gz = tiled::wrapn(z0 - C::HYZ + tz, g.n[2]);
-        const uint2 v = *reinterpret_cast<const uint2*>(occ + dev_row(g, grp, gz, gy) + x0 + 8 * chunk);
-        uint8_t* row = tile + tz * C::PS + ty * C::RS + 8 * chunk;
-        if constexpr (!C::PACK4) {
-          *reinterpret_cast<uint2*>(row + grp * C::XW) = v;
-        } else {
-          *reinterpret_cast<uint2*>(row + 2 * grp * C::XW) =
-              make_uint2((v.x & 0x0F0F0F0Fu) * C::W, (v.y & 0x0F0F0F0Fu) * C::W);
-          *reinterpret_cast<uint2*>(row + (2 * grp + 1) * C::XW) =
-              make_uint2(((v.x >> 4) & 0x0F0F0F0Fu) * C::W, ((v.y >> 4) & 0x0F0F0F0Fu) * C::W);
+      const int rpi = 32 / n8;
+      const int my_r = lane / n8, my_c = lane - (lane / n8) * n8;
+      const uint8_t* src0 = occ + x0 + 8 * my_c;
+      for (int base = warp * rpi; base < n_sub; base += NW * rpi) {
+        const int sub = base + my_r;
+        if (my_r < rpi && sub < n_sub) {
+          const int grp = sub % C::G;
+          const int t = sub / C::G;
+          const int ty = t % C::TY, tz = t / C::TY;
+          const int gy = pwrap(y0 - C::HYZ + ty, ny), gz = pwrap(z0 - C::HYZ + tz, nz);
+          const uint8_t* src = src0 + ((static_cast<size_t>(grp) * nz + gz) * ny + gy) * px;
+          uint8_t* row = tile + tz * C::PS + ty * C::RS + 8 * my_c;
+          if constexpr (!C::PACK4) {
+            const uint32_t dst = static_cast<uint32_t>(__cvta_generic_to_shared(row + grp * C::XW));
+            asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(dst), "l"(src) : "memory");
+          } else {
+            const uint2 v = *reinterpret_cast<const uint2*>(src);
+            *reinterpret_cast<uint2*>(row + 2 * grp * C::XW) =
+                make_uint2((v.x & 0x0F0F0F0Fu) * C::W, (v.y & 0x0F0F0F0Fu) * C::W);
+            *reinterpret_cast<uint2*>(row + (2 * grp + 1) * C::XW) =
+                make_uint2(((v.x >> 4) & 0x0F0F0F0Fu) * C::W, ((v.y >> 4) & 0x0F0F0F0Fu) * C::W);
+          }
         }
       }
     } else {
-      for (int item = tid; item < n_sub * ex; item += C::NT) {
-        const int tx = item % ex;
-        const int sub = item / ex;
+      for (int sub = warp; sub < n_sub; sub += NW) {
         const int grp = sub % C::G;
-        const int ty = (sub / C::G) % C::TY;
-        const int tz = sub / (C::G * C::TY);
-        const int gx = tiled::wrapn(x0 + tx, g.n[0]);
-        const int gy = tiled::wrapn(y0 - C::HYZ + ty, g.n[1]);
-        const int gz = tiled::wrapn(z0 - C::HYZ + tz, g.n[2]);
-        const uint8_t v = occ[dev_row(g, grp, gz, gy) + gx];
-        uint8_t* row = tile + tz * C::PS + ty * C::RS + tx;
-        if constexpr (!C::PACK4) {
-          row[grp * C::XW] = v;
-        } else {
-          row[2 * grp * C::XW] = static_cast<uint8_t>((v & 15) * C::W);
-          row[(2 * grp + 1) * C::XW] = static_cast<uint8_t>((v >> 4) * C::W);
+        const int t = sub / C::G;
+        const int ty = t % C::TY, tz = t / C::TY;
+        const int gy = pwrap(y0 - C::HYZ + ty, ny), gz = pwrap(z0 - C::HYZ + tz, nz);
+        const uint8_t* src = occ + ((static_cast<size_t>(grp) * nz + gz) * ny + gy) * px;
+        uint8_t* row = tile + tz * C::PS + ty * C::RS;
+        for (int tx = lane; tx < ex; tx += 32) {
+          const uint8_t v = src[pwrap(x0 + tx, nx)];
+          if constexpr (!C::PACK4) {
+            row[grp * C::XW + tx] = v;
+          } else {
+            row[2 * grp * C::XW + tx] = static_cast<uint8_t>((v & 15) * C::W);
+            row[(2 * grp + 1) * C::XW + tx] = static_cast<uint8_t>((v >> 4) * C::W);
+          }
         }
       }
     }
-    __syncthreads();
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+  };
 
+  int buf = 0;
+  if (static_cast<int>(blockIdx.x) < n_boxes) stage(blockIdx.x, tiles);
+  for (int box = blockIdx.x; box < n_boxes; box += gridDim.x, buf ^= 1) {
+    const int next = box + gridDim.x;
+    if (next < n_boxes) {
+      stage(next, tiles + (buf ^ 1) * C::TILE);  // prefetch while this box is counted
+      asm volatile("cp.async.wait_group 1;\n" ::: "memory");
+    } else {
+      asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+    }
+    __syncthreads();
+    const uint8_t* tile = tiles + buf * C::TILE;
+    const int x0 = (box % nbx) * C::BXC;
+    const int y0 = ((box / nbx) % nby) * C::BYC;
+    const int z0 = (box / (nbx * nby)) * C::BZC;
     // ---- count
     unsigned long long R[C::KMAX][C::M];
     auto clear = [&]() {
@@ -189,10 +219,10 @@ __global__ void __launch_bounds__(C::NT) k_pair_count_tiled(const Geom g,
         const uint32_t centre = *base;
 #pragma unroll
         for (int p = 0; p < C::KMAX; ++p) {
-          const unsigned long long mask =
-              centre == static_cast<uint32_t>(p * C::W) ? ~0ull : 0ull;
+          if (centre == static_cast<uint32_t>(p * C::W)) {  // one row: predicated adds
 #pragma unroll
-          for (int m = 0; m < C::M; ++m) R[p][m] += acc[m] & mask;
+            for (int m = 0; m < C::M; ++m) R[p][m] += acc[m];
+          }
         }
       }
     };
@@ -206,6 +236,7 @@ __global__ void __launch_bounds__(C::NT) k_pair_count_tiled(const Geom g,
       rows(std::integral_constant<int, 3>{});
     }
     flush();
+    __syncthreads();  // the next prefetch reuses this buffer
   }
   __syncthreads();
   for (int i = tid; i < C::NCNT; i += C::NT)
@@ -223,7 +254,7 @@ bool p_supported(const Geom& g) {
 template <class C>
 cudaError_t p_launch(const Geom& g, const uint8_t* occ, unsigned long long* hcnt, int n_sm,
                      cudaStream_t st) {
-  const size_t smem = round_up(4 * C::NCNT, 16) + C::TILE;
+  const size_t smem = round_up(4 * C::NCNT, 16) + 2 * C::TILE;
   cudaError_t e = cudaFuncSetAttribute(k_pair_count_tiled<C>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        static_cast<int>(smem));
