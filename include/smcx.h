@@ -171,8 +171,11 @@ smcx_status smcx_checkpoint(smcx_lattice* lat, void* buf, size_t* len);
 smcx_status smcx_restore(smcx_lattice* lat, const void* buf, size_t len);
 
 /* Tuning knobs (do not change results, only speed):
-     SMCX_OPT_KERNEL   0 = automatic, 1 = generic (global memory),
-                       2 = tiled (shared-memory tiles + halos)
+     SMCX_OPT_KERNEL   0 = automatic, 1 = generic (global memory, any lattice),
+                       2 = tiled (shared-memory tiles + halos, large lattices),
+                       3 = cell (one thread per link cell, n_d >= 4)
+                       (a sweep fails with EINVAL if the requested kernel
+                       cannot run the lattice)
      SMCX_OPT_TILE     index of the tile shape among smcx_tile_shape(...) */
 #define SMCX_OPT_KERNEL 1u
 #define SMCX_OPT_TILE 2u
@@ -184,8 +187,8 @@ uint32_t smcx_tile_shape_count(uint32_t kind);
 smcx_status smcx_tile_shape(uint32_t kind, uint32_t i, uint32_t* cells_xyz);
 
 /* Kernel the next sweep will use for this lattice and EPI: *kernel = 1
-   (generic, global memory) or 2 (tiled, shared-memory tiles + halos) and
-   *tile_shape = the tile shape index (-1 for the generic kernel).
+   (generic), 2 (tiled) or 3 (cell), 0 if the requested kernel cannot run
+   it, and *tile_shape = the tile shape index (-1 unless tiled).
    ESTATE: no EPI. */
 smcx_status smcx_kernel_in_use(smcx_lattice* lat, uint32_t* kernel, int32_t* tile_shape);
 

@@ -63,3 +63,17 @@ cudaError_t launch_pair_count_tiled(const Geom& g, int n_shells, const uint8_t* 
                                     unsigned long long* h, int n_sm, cudaStream_t st,
                                     bool check_only);
 }  // namespace smcx
+
+namespace smcx {
+// cell sweep phase (kernels_cell.cuh): any 8-bit lattice with K <= 6,
+// 2 <= M <= 4 and every n_d >= 4; dtab = the tiled kernel's difference rows
+bool cell_supported(const Geom& g);
+int cell_variant(const Geom& g);
+cudaError_t launch_sweep_cells(const Geom& g, const PhaseArgs& a, const Tables& tab, uint8_t* occ,
+                               const uint8_t* dtab, unsigned long long* stats, cudaStream_t st);
+// batched form: jobs = device array of cell::JobDev, blocks = (job, first cell)
+cudaError_t launch_sweep_cells_batch(int variant, const void* jobs, const uint2* blocks,
+                                     uint32_t n_blocks, uint32_t grid, uint32_t s, int colour,
+                                     cudaStream_t st);
+size_t cell_job_bytes();
+}  // namespace smcx

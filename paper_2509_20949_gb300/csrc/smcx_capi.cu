@@ -201,40 +201,64 @@ struct smcx_lattice {
   uint8_t* scratch() { return d_work + wl.scratch; }
   uint32_t* dtab() { return reinterpret_cast<uint32_t*>(d_work + wl.D); }
   unsigned int* flag() { return reinterpret_cast<unsigned int*>(stats() + kStatStatus); }
-  Geom geom() const {
-    Geom g;
-    g.kind = static_cast<int>(desc.kind);
-    g.nb = nb;
-    for (int c = 0; c < 3; ++c) {
-      g.n[c] = static_cast<int>(desc.n[c]);
-      g.m[c] = m[c];
-    }
-    g.L = L;
-    g.K = static_cast<int>(desc.n_species);
-    g.M = static_cast<int>(M);
-    g.z1 = shell_z(g.kind, 0);
-    g.pack4 = desc.pack_bits == 4;
-    g.px = static_cast<int>(row_pitch(&desc));
-    g.W = desc.pack_bits == 4 ? 1 : code_width(g.K);
-    g.seed_lo = static_cast<uint32_t>(desc.seed);
-    g.seed_hi = static_cast<uint32_t>(desc.seed >> 32);
-    for (int c = 0; c < 3; ++c) {
-      const uint32_t md = static_cast<uint32_t>(m[c]);
-      g.bq[c] = desc.n[c] / md;
-      g.br[c] = desc.n[c] % md;
-      g.bmag[c] = md == 1 ? 0xFFFFFFFFu
-                          : (md <= 1600 ? static_cast<uint32_t>(((1ull << 32) + md - 1) / md) : 0u);
-    }
-    uint32_t k0 = g.seed_lo, k1 = g.seed_hi;
-    for (int r = 0; r < 10; ++r) {
-      g.rk[r][0] = k0;
-      g.rk[r][1] = k1;
-      k0 += 0x9E3779B9u;
-      k1 += 0xBB67AE85u;
-    }
-    return g;
-  }
+  Geom geom() const;
 };
+
+namespace {
+
+Geom geom_of(const smcx_lattice_desc& desc, int M, int L, const int m[3]) {
+  Geom g;
+  g.kind = static_cast<int>(desc.kind);
+  g.nb = basis_count(g.kind);
+  for (int c = 0; c < 3; ++c) {
+    g.n[c] = static_cast<int>(desc.n[c]);
+    g.m[c] = m[c];
+  }
+  g.L = L;
+  g.K = static_cast<int>(desc.n_species);
+  g.M = M;
+  g.z1 = shell_z(g.kind, 0);
+  g.pack4 = desc.pack_bits == 4;
+  g.px = static_cast<int>(row_pitch(&desc));
+  g.W = desc.pack_bits == 4 ? 1 : code_width(g.K);
+  g.seed_lo = static_cast<uint32_t>(desc.seed);
+  g.seed_hi = static_cast<uint32_t>(desc.seed >> 32);
+  for (int c = 0; c < 3; ++c) {
+    const uint32_t md = static_cast<uint32_t>(m[c]);
+    g.bq[c] = desc.n[c] / md;
+    g.br[c] = desc.n[c] % md;
+    g.bmag[c] = md == 1 ? 0xFFFFFFFFu
+                        : (md <= 1600 ? static_cast<uint32_t>(((1ull << 32) + md - 1) / md) : 0u);
+  }
+  uint32_t k0 = g.seed_lo, k1 = g.seed_hi;
+  for (int r = 0; r < 10; ++r) {
+    g.rk[r][0] = k0;
+    g.rk[r][1] = k1;
+    k0 += 0x9E3779B9u;
+    k1 += 0xBB67AE85u;
+  }
+  return g;
+}
+
+// link cells: edge L = floor((1 + h_R)/2) + 1 (two same-colour cells then never
+// share a site one writes and the other reads), raised to min_cell; per
+// dimension the largest even count <= n/L, or 1.
+void layout_of(const smcx_lattice_desc& d, int M, int* L_out, int m[3]) {
+  const int hR = shell_reach(static_cast<int>(d.kind), M);
+  int L = (1 + hR) / 2 + 1;
+  if (static_cast<int>(d.min_cell) > L) L = static_cast<int>(d.min_cell);
+  *L_out = L;
+  for (int c = 0; c < 3; ++c) {
+    int cnt = static_cast<int>(d.n[c]) / L;
+    cnt &= ~1;
+    if (cnt < 2 || (d.flags & SMCX_SINGLE_CELL)) cnt = 1;
+    m[c] = cnt;
+  }
+}
+
+}  // namespace
+
+Geom smcx_lattice::geom() const { return geom_of(desc, static_cast<int>(M), L, m); }
 
 namespace {
 
@@ -270,21 +294,7 @@ ShellParam shell_param(int kind) {
   return sp;
 }
 
-// link cells: edge L = floor((1 + h_R)/2) + 1 (two same-colour cells then never
-// share a site one writes and the other reads), raised to min_cell; per
-// dimension the largest even count <= n/L, or 1.
-void compute_layout(smcx_lattice* lat) {
-  const int hR = shell_reach(static_cast<int>(lat->desc.kind), static_cast<int>(lat->M));
-  int L = (1 + hR) / 2 + 1;
-  if (static_cast<int>(lat->desc.min_cell) > L) L = static_cast<int>(lat->desc.min_cell);
-  lat->L = L;
-  for (int c = 0; c < 3; ++c) {
-    int cnt = static_cast<int>(lat->desc.n[c]) / L;
-    cnt &= ~1;
-    if (cnt < 2 || (lat->desc.flags & SMCX_SINGLE_CELL)) cnt = 1;
-    lat->m[c] = cnt;
-  }
-}
+void compute_layout(smcx_lattice* lat) { layout_of(lat->desc, static_cast<int>(lat->M), &lat->L, lat->m); }
 
 smcx_status validate_occupancy(const smcx_lattice_desc& d, const uint8_t* h) {
   const uint64_t N = n_sites(&d);
@@ -400,10 +410,18 @@ int tiled_shape_for(smcx_lattice* lat) {
   return -1;
 }
 
-// which kernel a colour phase runs: 1 = generic, 2 = tiled
+// which kernel a colour phase runs: 1 = generic, 2 = tiled, 3 = cell
 int kernel_choice(smcx_lattice* lat) {
-  if (lat->opt_kernel == 1) return 1;
-  return tiled_shape_for(lat) >= 0 ? 2 : 1;
+  const Geom g = lat->geom();
+  const bool cell_ok = lat->tiled_table_ok && cell_supported(g);
+  switch (lat->opt_kernel) {
+    case 1: return 1;
+    case 2: return tiled_shape_for(lat) >= 0 ? 2 : 0;
+    case 3: return cell_ok ? 3 : 0;
+    default:
+      if (tiled_shape_for(lat) >= 0) return 2;
+      return cell_ok ? 3 : 1;
+  }
 }
 
 // one colour phase of the current sweep
@@ -414,8 +432,14 @@ smcx_status launch_colour(smcx_lattice* lat, int colour, const PhaseArgs& base, 
   for (int d = 0; d < 3; ++d)
     if (g.m[d] == 1 && ((colour >> d) & 1)) return SMCX_OK;  // no cell of this colour
   const int kern = kernel_choice(lat);
-  if (lat->opt_kernel == 2 && kern != 2)
-    return fail(SMCX_EINVAL, "the tiled kernel does not support this lattice/EPI/tile shape");
+  if (kern == 0)
+    return fail(SMCX_EINVAL, "the requested kernel does not support this lattice/EPI/tile shape");
+  if (kern == 3) {
+    SMCX_CUDA(lat, launch_sweep_cells(g, a, tab, lat->d_occ,
+                                      reinterpret_cast<const uint8_t*>(lat->dtab()), lat->stats(),
+                                      lat->stream));
+    return SMCX_OK;
+  }
   if (kern == 2) {
     TiledEpi te;
     te.kmax = lat->tiled_kmax;
@@ -435,18 +459,18 @@ smcx_status launch_colour(smcx_lattice* lat, int colour, const PhaseArgs& base, 
 // s = 1..K-1 with D_{m,s} = V_m(q,s) - V_m(p,s), then the int64 constant
 // C = [32 sum_{m,s} D'_{m,s} when K <= 5] + D_{1,q} - D_{1,p}.  Returns false
 // when a D' does not fit int32.
-bool build_tiled_table(smcx_lattice* lat, std::vector<uint32_t>* out) {
-  const int K = static_cast<int>(lat->desc.n_species);
-  const int M = static_cast<int>(lat->M);
+bool dtable_of(const smcx_lattice_desc& d, int M, const int64_t* Vt, std::vector<uint8_t>* bytes,
+               int* kmax_out) {
+  const int K = static_cast<int>(d.n_species);
   if (K > 6 || M < 2) return false;
   const int kmax = K <= 5 ? 5 : 6;
   const int rowb = tiled_row_bytes(M, kmax);
   const int doff = tiled_doff_c(M, kmax);
-  std::vector<uint8_t> bytes(static_cast<size_t>(kmax) * kmax * rowb, 0);
-  auto V = [&](int m, int a, int b) { return lat->V[(static_cast<size_t>(m) * K + a) * K + b]; };
+  bytes->assign(static_cast<size_t>(kmax) * kmax * rowb, 0);
+  auto V = [&](int m, int a, int b) { return Vt[(static_cast<size_t>(m) * K + a) * K + b]; };
   for (int p = 0; p < K; ++p)
     for (int q = 0; q < K; ++q) {
-      uint8_t* row = bytes.data() + static_cast<size_t>(p * kmax + q) * rowb;
+      uint8_t* row = bytes->data() + static_cast<size_t>(p * kmax + q) * rowb;
       __int128 C = 0;
       for (int m = 0; m < M; ++m) {
         const int64_t d0 = V(m, q, 0) - V(m, p, 0);
@@ -463,6 +487,14 @@ bool build_tiled_table(smcx_lattice* lat, std::vector<uint32_t>* out) {
       const int64_t c64 = static_cast<int64_t>(C);
       std::memcpy(row + doff, &c64, 8);
     }
+  if (kmax_out) *kmax_out = kmax;
+  return true;
+}
+
+bool build_tiled_table(smcx_lattice* lat, std::vector<uint32_t>* out) {
+  std::vector<uint8_t> bytes;
+  int kmax = 0;
+  if (!dtable_of(lat->desc, static_cast<int>(lat->M), lat->V.data(), &bytes, &kmax)) return false;
   out->assign(bytes.size() / 4, 0u);
   std::memcpy(out->data(), bytes.data(), bytes.size());
   lat->tiled_kmax = kmax;
@@ -491,6 +523,22 @@ uint32_t crc32(const uint8_t* p, size_t n, uint32_t crc = 0) {
 }
 
 }  // namespace
+
+namespace smcx {
+smcx_status batch_fail(smcx_status s, const std::string& msg) { return fail(s, msg); }
+bool host_build_tables(double T, Tables* tab, int* mode, int* s) { return build_tables(T, tab, mode, s); }
+Geom host_geom(const smcx_lattice_desc& d, int M, const int m[3]) {
+  int L = 0, mm[3];
+  layout_of(d, M, &L, mm);
+  return geom_of(d, M, L, m);
+}
+void host_layout(const smcx_lattice_desc& d, int M, int* L, int m[3]) { layout_of(d, M, L, m); }
+bool host_dtable(const smcx_lattice_desc& d, int M, const int64_t* V, std::vector<uint8_t>* out) {
+  return dtable_of(d, M, V, out, nullptr);
+}
+size_t host_occ_bytes(const smcx_lattice_desc& d) { return occ_bytes(&d); }
+bool host_desc_ok(const smcx_lattice_desc* d, std::string* why) { return desc_ok(d, why); }
+}  // namespace smcx
 
 extern "C" {
 
@@ -804,7 +852,7 @@ smcx_status smcx_restore(smcx_lattice* lat, const void* buf, size_t len) {
 smcx_status smcx_set_option(smcx_lattice* lat, uint32_t key, int64_t value) {
   if (!lat) return fail(SMCX_EINVAL, "null handle");
   if (key == SMCX_OPT_KERNEL) {
-    if (value < 0 || value > 2) return fail(SMCX_EINVAL, "kernel option must be 0..2");
+    if (value < 0 || value > 3) return fail(SMCX_EINVAL, "kernel option must be 0..3");
     lat->opt_kernel = static_cast<int>(value);
     return SMCX_OK;
   }

@@ -47,6 +47,7 @@ def write_region_sites(orc, desc, t, cids):
     n = desc.n
     out = []
     for cid in cids:
+        cid = int(cid)
         c = (cid % m[0], (cid // m[0]) % m[1], cid // (m[0] * m[1]))
         rng = []
         for d in range(3):
