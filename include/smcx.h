@@ -198,6 +198,68 @@ smcx_status smcx_destroy(smcx_lattice* lat);
 /* Text of the last error of this host thread ("" if none). */
 const char* smcx_last_error(void);
 
+/* ---- batched execution ---------------------------------------------------
+   Many independent lattices (the paper's temperature parallelism, Sec. 2.2:
+   simulations at different temperatures or compositions share nothing) run
+   together: every sweep's colour phases of all active jobs go out as a few
+   launches, a chunk of sweeps as one CUDA graph.  Each job's trajectory is
+   bit-identical to the same lattice run alone through smcx_sweep (same
+   seed, temperature and sweep counter).  Jobs use 8-bit storage, K <= 6,
+   2..4 shells, n >= 4 per dimension, a constant temperature.
+
+   Memory: the caller provides one device arena (256-byte aligned); its first
+   smcx_batch_control_bytes(max_jobs, transfer_bytes) bytes hold tables and a
+   transfer buffer of transfer_bytes (>= the largest job's site count), the
+   rest is the job heap.  No other device memory is used. */
+typedef struct smcx_batch smcx_batch;
+
+/* Bytes of the arena's control area; 0 for max_jobs == 0. */
+size_t smcx_batch_control_bytes(uint32_t max_jobs, size_t transfer_bytes);
+
+/* Heap bytes one job of this descriptor occupies (0 if invalid). */
+size_t smcx_batch_job_bytes(const smcx_lattice_desc* desc);
+
+/* Binds the arena and the stream (a cudaStream_t; with a non-NULL stream
+   chunks are captured into CUDA graphs).  ENOMEM: arena smaller than the
+   control area. */
+smcx_status smcx_batch_create(uint32_t max_jobs, void* d_arena, size_t arena_bytes,
+                              size_t transfer_bytes, void* cuda_stream, smcx_batch** out);
+
+/* Admits a job: occupancy h_init (canonical, N bytes), EPI [n_shells][K][K]
+   (q units, symmetric), temperature T (kelvin, constant), n_sweeps to run.
+   The job starts at sweep counter 0 and joins the next smcx_batch_run.
+   *job_id receives its id (a slot index, reused after smcx_batch_remove).
+   EBUDGET: no free slot or no room left in the arena.  EINVAL: invalid or
+   unsupported job. */
+smcx_status smcx_batch_add(smcx_batch* b, const smcx_lattice_desc* desc, const uint8_t* h_init,
+                           uint32_t n_shells, const int64_t* v_q, double T, uint32_t n_sweeps,
+                           uint32_t* job_id);
+
+/* Runs up to chunk_sweeps sweeps of every active job (fewer for jobs that
+   finish inside the chunk) and synchronises.  *n_finished (may be NULL)
+   receives the number of jobs that completed in this chunk. */
+smcx_status smcx_batch_run(smcx_batch* b, uint32_t chunk_sweeps, uint32_t* n_finished);
+
+/* Pops up to cap ids of finished jobs (completion order) into ids; *n gets
+   the count. */
+smcx_status smcx_batch_poll(smcx_batch* b, uint32_t* ids, uint32_t cap, uint32_t* n);
+
+/* Result of a job (finished or not): occupancy (canonical, N bytes; h_occ
+   may be NULL), cumulative trial statistics, running energy (q units) and
+   sweeps done.  Synchronises. */
+smcx_status smcx_batch_result(smcx_batch* b, uint32_t job_id, uint8_t* h_occ,
+                              smcx_sweep_stats* totals, int64_t* e_run, uint32_t* sweeps_done);
+
+/* Releases a job's slot and heap space. */
+smcx_status smcx_batch_remove(smcx_batch* b, uint32_t job_id);
+
+/* Occupancy of the batch: running jobs, free slots, free heap bytes and the
+   largest free block. */
+smcx_status smcx_batch_info(smcx_batch* b, uint32_t* active, uint32_t* free_slots,
+                            size_t* free_bytes, size_t* largest_free);
+
+smcx_status smcx_batch_destroy(smcx_batch* b);
+
 /* Shell table used by the library: writes up to cap vectors (dx,dy,dz in
    half units) of shells 1..n_shells, sorted by distance then
    lexicographically, and z[m]; returns the number of vectors, 0 on error. */

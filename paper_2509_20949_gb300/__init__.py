@@ -9,11 +9,14 @@ it cannot.
 """
 from ._lib import SmcxError, build, lib  # noqa: F401
 
-__all__ = ["Lattice", "SmcxError", "build", "lib"]
+__all__ = ["Lattice", "Batch", "SmcxError", "build", "lib"]
 
 
 def __getattr__(name):
     if name == "Lattice":
         from .lattice import Lattice
         return Lattice
+    if name == "Batch":
+        from .batch import Batch
+        return Batch
     raise AttributeError(name)

@@ -138,6 +138,19 @@ SIGNATURES = {
     "smcx_last_error": (ctypes.c_char_p, []),
     "smcx_shell_table": (ctypes.c_uint32, [ctypes.c_uint32, ctypes.c_uint32, _P(ctypes.c_int32),
                                            ctypes.c_uint32, _P(ctypes.c_uint32)]),
+    "smcx_batch_control_bytes": (ctypes.c_size_t, [ctypes.c_uint32, ctypes.c_size_t]),
+    "smcx_batch_job_bytes": (ctypes.c_size_t, [_P(LatticeDesc)]),
+    "smcx_batch_create": (_st, [ctypes.c_uint32, _vp, ctypes.c_size_t, ctypes.c_size_t, _vp, _P(_vp)]),
+    "smcx_batch_add": (_st, [_vp, _P(LatticeDesc), _vp, ctypes.c_uint32, _vp, ctypes.c_double,
+                             ctypes.c_uint32, _P(ctypes.c_uint32)]),
+    "smcx_batch_run": (_st, [_vp, ctypes.c_uint32, _P(ctypes.c_uint32)]),
+    "smcx_batch_poll": (_st, [_vp, _P(ctypes.c_uint32), ctypes.c_uint32, _P(ctypes.c_uint32)]),
+    "smcx_batch_result": (_st, [_vp, ctypes.c_uint32, _vp, _P(SweepStats), _P(ctypes.c_int64),
+                                _P(ctypes.c_uint32)]),
+    "smcx_batch_remove": (_st, [_vp, ctypes.c_uint32]),
+    "smcx_batch_info": (_st, [_vp, _P(ctypes.c_uint32), _P(ctypes.c_uint32), _P(ctypes.c_size_t),
+                              _P(ctypes.c_size_t)]),
+    "smcx_batch_destroy": (_st, [_vp]),
     "smcx_philox4x32_10": (None, [_P(ctypes.c_uint32), _P(ctypes.c_uint32), _P(ctypes.c_uint32)]),
     "smcx_philox_device": (_st, [ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32,
                                  ctypes.c_uint64, ctypes.c_uint32, _vp, _vp]),

@@ -1,0 +1,111 @@
+"""Batched execution (smcx_batch_*): every job's trajectory equals the same
+lattice run alone through smcx_sweep, and the oracle, bit for bit; jobs can
+join and leave between chunks; admission respects the arena budget."""
+import numpy as np
+import pytest
+
+from paper_2509_20949_gb300 import inputs
+from tests.gpu_util import make_case, require_cuda
+
+pytestmark = pytest.mark.gpu
+
+
+def _jobs(seed, count, nmin=4, nmax=14):
+    rng = np.random.default_rng(seed)
+    jobs = []
+    for j in range(count):
+        kind = int(rng.integers(0, 2))
+        n = tuple(int(v) for v in rng.integers(nmin, nmax + 1, 3))
+        K = int(rng.integers(2, 7))
+        M = int(rng.integers(2, 5))
+        T = float(rng.choice([0.0, 300.0 + 1200.0 * rng.uniform(), float("inf")], p=[0.1, 0.8, 0.1]))
+        case = make_case(kind, n, K, M, seed=100 + j, sigma=0.03, epi_seed=200 + j, occ_seed=300 + j)
+        case.update(T=T, sweeps=int(rng.integers(1, 25)))
+        jobs.append(case)
+    return jobs
+
+
+def _alone(case):
+    from paper_2509_20949_gb300.lattice import Lattice
+    lat = Lattice(case["kind"], case["n"], case["K"], case["occ"], seed=case["seed"])
+    lat.set_epi(case["V"])
+    st = lat.sweep(case["sweeps"], case["T"])
+    return lat.occupancy(), st, lat.running_energy()
+
+
+def _batch(max_jobs=64, arena=1 << 26, transfer=1 << 20):
+    from paper_2509_20949_gb300.batch import Batch
+    return Batch(max_jobs, arena, transfer)
+
+
+def _add(b, case):
+    return b.add(case["kind"], case["n"], case["K"], case["occ"], case["V"], case["T"],
+                 case["sweeps"], seed=case["seed"])
+
+
+def test_batch_matches_alone_and_oracle(orc):
+    require_cuda()
+    jobs = _jobs(1, 14)
+    b = _batch()
+    ids = [_add(b, c) for c in jobs]
+    done = set()
+    for _ in range(40):
+        b.run(6)
+        done |= set(b.poll())
+        if len(done) == len(jobs):
+            break
+    assert done == set(ids)
+    for jid, c in zip(ids, jobs):
+        r = b.result(jid)
+        occ, st, E = _alone(c)
+        assert np.array_equal(r["occ"], occ), jid
+        assert r["stats"] == st and r["energy"] == E and r["sweeps"] == c["sweeps"]
+    # the oracle for a few of them
+    for jid, c in list(zip(ids, jobs))[:4]:
+        d = orc.Desc(c["kind"], c["n"], c["K"], c["M"], seed=c["seed"])
+        o_occ, _ = orc.sweeps(d, c["V"], c["occ"], 0, c["sweeps"], c["T"])
+        assert np.array_equal(b.result(jid)["occ"], o_occ)
+
+
+def test_jobs_join_and_leave_between_chunks():
+    require_cuda()
+    jobs = _jobs(2, 12)
+    b = _batch(max_jobs=5)
+    pending = list(range(len(jobs)))
+    running = {}
+    finished = {}
+    chunks = 0
+    while pending or running:
+        while pending and b.info()["free_slots"] > 0:
+            k = pending.pop(0)
+            running[_add(b, jobs[k])] = k
+        b.run(4)
+        chunks += 1
+        for jid in b.poll():
+            k = running.pop(jid)
+            finished[k] = b.result(jid)
+            b.remove(jid)
+        assert chunks < 200
+    for k, c in enumerate(jobs):
+        occ, st, E = _alone(c)
+        assert np.array_equal(finished[k]["occ"], occ), k
+        assert finished[k]["stats"] == st and finished[k]["energy"] == E
+
+
+def test_admission_budget():
+    require_cuda()
+    from paper_2509_20949_gb300 import SmcxError
+    from paper_2509_20949_gb300.batch import Batch
+    case = make_case(0, (16, 16, 16), 4, 3, seed=1)
+    case.update(T=800.0, sweeps=3)
+    per_job = Batch.job_bytes(0, (16, 16, 16), 4)
+    ctrl = Batch.control_bytes(8, 1 << 16)
+    b = Batch(8, ctrl + 2 * per_job, 1 << 16)
+    a = _add(b, case)
+    _add(b, case)
+    assert b.try_add(case["kind"], case["n"], case["K"], case["occ"], case["V"], 800.0, 3) is None
+    b.remove(a)
+    assert b.info()["free_bytes"] >= per_job
+    _add(b, case)
+    with pytest.raises(SmcxError):
+        b.add(0, (3, 4, 4), 3, np.zeros(96, np.uint8), inputs.epi_table(2, 3, 0.02, 0), 500.0, 1)
