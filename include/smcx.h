@@ -260,6 +260,38 @@ smcx_status smcx_batch_info(smcx_batch* b, uint32_t* active, uint32_t* free_slot
 
 smcx_status smcx_batch_destroy(smcx_batch* b);
 
+/* ---- pair counts without allocation ---------------------------------------
+   (No counterpart in the paper: an interface for callers that cannot
+   allocate device memory where they need the counts -- code running inside
+   another framework's memory-pool callbacks or allocator hooks, where a
+   nested allocation would recurse or deadlock; processes whose device memory
+   is wholly reserved by their host framework; deployments that forbid
+   allocation after start-up.)
+
+   Computes the same directed shell pair counts N_m[p'][p] as
+   smcx_warren_cowley_sro, from a caller's device occupancy in the canonical
+   layout (d_canon, N bytes), into the caller's device array d_counts
+   ([n_shells][K][K] uint64), enqueued on cuda_stream (a cudaStream_t,
+   NULL = legacy default stream); the call does not synchronise.  It needs
+   no handle and no workspace and never allocates: its accumulators live in
+   a static device array of the library holding SMCX_NOALLOC_MAX_SHELLS x
+   SMCX_NOALLOC_MAX_SPECIES^2 counters (8 KiB), which every GPU that loads
+   the library keeps until the process exits.  The first call on a device
+   looks up that array's device address (cudaGetSymbolAddress) with the
+   device current; make it before any stream capture.  All calls on a device
+   share the array, which is cleared at the start of each call and keeps the
+   last call's counts afterwards: calls whose work overlaps on the GPU (other
+   streams, other threads) race and must be serialised by the caller.  Pairs
+   involving a site whose id is >= n_species are not counted.
+   EINVAL: kind not BCC/FCC, n_species > 16, n_shells outside 1..4, a size
+   of 0, 2^32 or more sites, or a null pointer.  ECUDA: symbol lookup or
+   launch failed. */
+#define SMCX_NOALLOC_MAX_SHELLS 4
+#define SMCX_NOALLOC_MAX_SPECIES 16
+smcx_status smcx_pair_counts_noalloc(uint32_t kind, const uint32_t* n, uint32_t n_species,
+                                     uint32_t n_shells, const uint8_t* d_canon, uint64_t* d_counts,
+                                     void* cuda_stream);
+
 /* Shell table used by the library: writes up to cap vectors (dx,dy,dz in
    half units) of shells 1..n_shells, sorted by distance then
    lexicographically, and z[m]; returns the number of vectors, 0 on error. */

@@ -151,6 +151,8 @@ SIGNATURES = {
     "smcx_batch_info": (_st, [_vp, _P(ctypes.c_uint32), _P(ctypes.c_uint32), _P(ctypes.c_size_t),
                               _P(ctypes.c_size_t)]),
     "smcx_batch_destroy": (_st, [_vp]),
+    "smcx_pair_counts_noalloc": (_st, [ctypes.c_uint32, _P(ctypes.c_uint32), ctypes.c_uint32,
+                                       ctypes.c_uint32, _vp, _vp, _vp]),
     "smcx_philox4x32_10": (None, [_P(ctypes.c_uint32), _P(ctypes.c_uint32), _P(ctypes.c_uint32)]),
     "smcx_philox_device": (_st, [ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32,
                                  ctypes.c_uint64, ctypes.c_uint32, _vp, _vp]),
