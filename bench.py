@@ -51,6 +51,14 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--mode", default="plain", choices=["plain", "batch", "serve"],
+                    help="plain: the single-lattice sweep (default); batch: 256 independent "
+                         "lattices batched vs one at a time; serve: Poisson-arrival serving")
+    ap.add_argument("--jobs", type=int, default=256)
+    ap.add_argument("--chunk", type=int, default=50)
+    ap.add_argument("--rate", type=float, default=5.0)
+    ap.add_argument("--window", type=float, default=10.0)
+    ap.add_argument("--budget-gb", type=float, default=160.0)
     return ap.parse_args()
 
 
@@ -217,10 +225,100 @@ def run_reference(args):
     return 0
 
 
+def _job_arrays(j):
+    V = inputs.epi_table(j["M"], j["K"], j["sigma"], j["epi_seed"])
+    occ = inputs.initial_occupancy(j["kind"], j["n"], j["K"], j["occ_seed"], j["fractions"])
+    return V, occ
+
+
+def run_batch(args):
+    """256 independent lattices (n ~ log-U(8, 64) conventional cells, BCC/FCC,
+    K ~ U{3..6}, shells 1-3, T ~ U(300, 1500) K, 200 sweeps each): batched
+    (one graph-captured chunk of sweeps for all jobs) vs one job at a time
+    through smcx_sweep.  Both with the lattices already on the device."""
+    import torch
+
+    from paper_2509_20949_gb300.batch import Batch
+    from paper_2509_20949_gb300.lattice import Lattice
+
+    torch.cuda.set_device(0)
+    jobs = inputs.batch_jobs(args.jobs)
+    arrays = [_job_arrays(j) for j in jobs]
+    total_sites = sum(inputs.n_sites(j["kind"], j["n"]) for j in jobs)
+    attempts = sum(inputs.n_sites(j["kind"], j["n"]) * j["sweeps"] for j in jobs)
+    heap = sum(Batch.job_bytes(j["kind"], j["n"], j["K"]) for j in jobs)
+    transfer = max(inputs.n_sites(j["kind"], j["n"]) for j in jobs)
+    b = Batch(len(jobs), Batch.control_bytes(len(jobs), transfer) + heap + (1 << 20), transfer)
+    ids = [b.add(j["kind"], j["n"], j["K"], occ, V, j["T_first"], j["sweeps"], seed=j["seed"])
+           for j, (V, occ) in zip(jobs, arrays)]
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    done = 0
+    while done < len(ids):
+        b.run(args.chunk)
+        done += len(b.poll())
+    torch.cuda.synchronize()
+    t_batch = time.perf_counter() - t0
+    # one job at a time (device-resident lattices, each job's sweeps timed)
+    lats = []
+    for j, (V, occ) in zip(jobs, arrays):
+        lat = Lattice(j["kind"], j["n"], j["K"], occ, seed=j["seed"])
+        lat.set_epi(V)
+        lats.append(lat)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for j, lat in zip(jobs, lats):
+        lat.sweep(j["sweeps"], j["T_first"], stats=False)
+    torch.cuda.synchronize()
+    t_single = time.perf_counter() - t0
+    same = all(np.array_equal(b.result(i)["occ"], lat.occupancy())
+               for i, lat in list(zip(ids, lats))[:: max(1, len(ids) // 16)])
+    line = {"metric": "attempted MC swaps/sec on 1 GB300 (batched, 256 independent lattices)",
+            "value": attempts / t_batch, "unit": UNIT, "n_gpus": 1, "higher_is_better": True,
+            "one_at_a_time": attempts / t_single, "speedup": t_single / t_batch,
+            "identical_results_sampled": bool(same),
+            "config": {"workload": f"{len(jobs)} jobs, {total_sites} sites, {attempts} trials, "
+                                   f"chunk {args.chunk} sweeps", "dtype": "int64"}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_serve(args):
+    """Poisson arrivals (rate per s, window s) of lattices with 1e4-1e8 sites
+    and 100-5000 sweeps (log-uniform), composition or temperature scans,
+    admitted by an HBM budget, continuous batching; p50/p99 latency of the
+    completed jobs and aggregate swaps/s."""
+    import torch
+
+    from paper_2509_20949_gb300.server import Server
+
+    torch.cuda.set_device(0)
+    trace = inputs.served_jobs(args.rate, args.window, seed=11)
+    for j in trace:
+        j["V"], j["occ"] = _job_arrays(j)
+    budget = int(args.budget_gb * (1 << 30))
+    srv = Server(budget, max_jobs=1024, chunk_sweeps=args.chunk, transfer_bytes=(1 << 27))
+    m = srv.run_trace(trace, deadline_s=args.window * 3)
+    line = {"metric": "attempted MC swaps/sec on 1 GB300 (served, continuous batching)",
+            "value": m["swaps_per_s"], "unit": UNIT, "n_gpus": 1, "higher_is_better": True,
+            "p50_latency_s": m["p50_latency_s"], "p99_latency_s": m["p99_latency_s"],
+            "completed": m["completed"], "submitted": m["submitted"],
+            "completed_fraction": m["completed_fraction"], "elapsed_s": m["elapsed_s"],
+            "config": {"workload": f"Poisson {args.rate}/s over {args.window} s, sites log-U(1e4,1e8), "
+                                   f"sweeps log-U(100,5000), budget {args.budget_gb} GB, "
+                                   f"chunk {args.chunk}", "dtype": "int64"}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.mode == "batch":
+        return run_batch(args)
+    if args.mode == "serve":
+        return run_serve(args)
     import torch
 
     world, rank, local = dist_setup()

@@ -179,5 +179,5 @@ def served_jobs(rate_per_s: float, window_s: float, seed: int, n_sites_min: floa
         T = float(rng.uniform(300.0, 1500.0))
         jobs.append(dict(job=j, arrival_s=t, kind=kind, n=(n, n, n), K=K, M=3, sigma=0.02,
                          epi_seed=5000 + j, seed=5000 + j, occ_seed=5000 + j,
-                         fractions=fractions, T_first=T, T_last=T, sweeps=sweeps))
+                         fractions=fractions, T=T, T_first=T, T_last=T, sweeps=sweeps))
     return jobs
