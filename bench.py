@@ -142,6 +142,25 @@ def measured_peaks():
     return 6800.0, "fallback"
 
 
+def max_over_ranks(value: float) -> float:
+    """Maximum of a per-rank float over all ranks (identity without a process
+    group); NCCL reduces on the device, gloo on the host."""
+    import torch
+    import torch.distributed as dist
+
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(value)
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(value)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_seed(base_seed: int, rank: int) -> int:
+    """Each rank simulates an independent replica of the lattice."""
+    return int(base_seed) + int(rank)
+
+
 def dist_setup():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -333,7 +352,7 @@ def main():
     w, N, desc = workload_config(args.workload)
     V = inputs.epi_table(w["M"], w["K"], w["sigma"], w["epi_seed"])
     occ = inputs.initial_occupancy(w["kind"], w["n"], w["K"], w["occ_seed"], w["fractions"])
-    seed = w["seed"] + rank  # independent replica per rank
+    seed = replica_seed(w["seed"], rank)
     stream = torch.cuda.current_stream()
     lat = Lattice(w["kind"], w["n"], w["K"], occ, seed=seed, pack_bits=args.pack_bits,
                   stream=stream)
@@ -372,10 +391,7 @@ def main():
     clk = clocks.stop()
     t_ms = ev0.elapsed_time(ev1)
     sweep_ms = sum(a.elapsed_time(b) for a, b in ev_sweep)
-    if world > 1:
-        tt = torch.tensor([t_ms], device="cuda")
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        t_ms = float(tt.item())
+    t_ms = max_over_ranks(t_ms)
     total_attempts = N * args.steps * world
     value = total_attempts / (t_ms / 1e3)
     launches_per_sweep = 8
@@ -400,14 +416,12 @@ def main():
     e2e_s = time.perf_counter() - t0
     e2e_value = N * args.e2e_steps / e2e_s
     if world > 1:
-        tt = torch.tensor([e2e_s], device="cuda")
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        e2e_value = N * args.e2e_steps * world / float(tt.item())
+        e2e_value = N * args.e2e_steps * world / max_over_ranks(e2e_s)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(w, N, V, occ, args.cpu_seconds, rank)
-    traffic = _recorded_traffic()
+    traffic = _recorded_traffic() if args.workload == "bcc812_k5" and args.pack_bits == 8 else None
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -433,7 +447,23 @@ def main():
 
 
 def _recorded_traffic():
-    return None
+    """DRAM bytes per phase launch of the tiled sweep from the committed ncu
+    summary, if it was taken on the current kernel source (else None)."""
+    import hashlib
+    import re
+
+    prof = os.path.join(ROOT, "profiles", "sweep_tiled_bcc812_k5.md")
+    src = os.path.join(ROOT, "paper_2509_20949_gb300", "csrc", "kernels_tiled.cuh")
+    try:
+        text = open(prof).read()
+        sha = hashlib.sha1(open(src, "rb").read()).hexdigest()[:12]
+    except OSError:
+        return None
+    m_sha = re.search(r"source_sha1 \(.*?\): ([0-9a-f]+)", text)
+    m_b = re.search(r"dram_bytes_per_launch: ([0-9]+)", text)
+    if not m_sha or not m_b or m_sha.group(1) != sha:
+        return None
+    return int(m_b.group(1))
 
 
 if __name__ == "__main__":
