@@ -201,11 +201,18 @@ const char* smcx_last_error(void);
 /* ---- batched execution ---------------------------------------------------
    Many independent lattices (the paper's temperature parallelism, Sec. 2.2:
    simulations at different temperatures or compositions share nothing) run
-   together: every sweep's colour phases of all active jobs go out as a few
-   launches, a chunk of sweeps as one CUDA graph.  Each job's trajectory is
+   together.  Work items are 32 active link cells of one job and colour
+   phase, one per lane of a warp.  Two schedules: a chunk of sweeps of all
+   active jobs as one launch of a persistent kernel whose warps take items
+   from a queue in phase order, a per-job counter of finished items keeping
+   each job's colour phases in sequence (bounded waits: a wait that gives up
+   fails the run with ETIMEOUT); or one launch per colour phase covering all
+   jobs.  The schedule, item shape and register budget are tuned online.
+   With a stream the chunk is captured into a CUDA graph.  Each job's trajectory is
    bit-identical to the same lattice run alone through smcx_sweep (same
-   seed, temperature and sweep counter).  Jobs use 8-bit storage, K <= 6,
-   2..4 shells, n >= 4 per dimension, a constant temperature.
+   seed, temperature and sweep counter), whatever the tuning.  Jobs use 8-bit
+   storage, K <= 6, 2..4 shells, n >= 4 per dimension, a constant
+   temperature.
 
    Memory: the caller provides one device arena (256-byte aligned); its first
    smcx_batch_control_bytes(max_jobs, transfer_bytes) bytes hold tables and a
@@ -237,8 +244,42 @@ smcx_status smcx_batch_add(smcx_batch* b, const smcx_lattice_desc* desc, const u
 
 /* Runs up to chunk_sweeps sweeps of every active job (fewer for jobs that
    finish inside the chunk) and synchronises.  *n_finished (may be NULL)
-   receives the number of jobs that completed in this chunk. */
+   receives the number of jobs that completed in this chunk.  While the
+   batch is untuned, the first sweeps run as short timed sub-chunks, one per
+   tuning candidate (results are unaffected).  ETIMEOUT: a device-side wait
+   gave up (the batch then stays in an error state). */
 smcx_status smcx_batch_run(smcx_batch* b, uint32_t chunk_sweeps, uint32_t* n_finished);
+
+/* Tuning of the batched sweep (never changes results):
+     SMCX_BATCH_OPT_TILE       work-item shape index (see smcx_batch_tile_shape)
+     SMCX_BATCH_OPT_SCHEDULE   0 = persistent work queue (one launch per
+                               chunk, per-job phase counters), 1 = one launch
+                               per colour phase for all jobs
+     SMCX_BATCH_OPT_OCCUPANCY  register budget index: 0, 1 = 3, 4 resident
+                               blocks of 128 threads per SM
+   Value -1 (the default) = chosen online.  Setting any restarts the online
+   tuning. */
+#define SMCX_BATCH_OPT_TILE 1u
+#define SMCX_BATCH_OPT_OCCUPANCY 2u
+#define SMCX_BATCH_OPT_SCHEDULE 3u
+smcx_status smcx_batch_set_option(smcx_batch* b, uint32_t key, int64_t value);
+
+/* Current choice: *tile, *schedule and *occupancy (-1 while tuning), *tuned
+   = 1 once the online tuning has finished.  Any pointer may be NULL. */
+smcx_status smcx_batch_tuning(smcx_batch* b, int32_t* tile, int32_t* schedule, int32_t* occupancy,
+                              uint32_t* tuned);
+
+/* Work-queue statistics since the batch was created: out[0] = work items
+   that had to wait for the previous colour phase of their job, out[1] =
+   polls of those waits, out[2] = nanoseconds they waited (summed over
+   warps).  Synchronises. */
+smcx_status smcx_batch_queue_stats(smcx_batch* b, uint64_t* out);
+
+/* Active link cells (x, y, z) of work-item shape i (product 32): shape 0
+   is 32 consecutive cells of a colour in x-fastest order (rows wrap, so
+   (32, 1, 1) only when a row has >= 32), shapes 1..3 are boxes.  EINVAL for
+   i >= 4. */
+smcx_status smcx_batch_tile_shape(uint32_t i, uint32_t* cells_xyz);
 
 /* Pops up to cap ids of finished jobs (completion order) into ids; *n gets
    the count. */

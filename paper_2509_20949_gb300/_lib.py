@@ -151,6 +151,11 @@ SIGNATURES = {
     "smcx_batch_info": (_st, [_vp, _P(ctypes.c_uint32), _P(ctypes.c_uint32), _P(ctypes.c_size_t),
                               _P(ctypes.c_size_t)]),
     "smcx_batch_destroy": (_st, [_vp]),
+    "smcx_batch_set_option": (_st, [_vp, ctypes.c_uint32, ctypes.c_int64]),
+    "smcx_batch_tuning": (_st, [_vp, _P(ctypes.c_int32), _P(ctypes.c_int32), _P(ctypes.c_int32),
+                                _P(ctypes.c_uint32)]),
+    "smcx_batch_tile_shape": (_st, [ctypes.c_uint32, _P(ctypes.c_uint32)]),
+    "smcx_batch_queue_stats": (_st, [_vp, _P(ctypes.c_uint64)]),
     "smcx_pair_counts_noalloc": (_st, [ctypes.c_uint32, _P(ctypes.c_uint32), ctypes.c_uint32,
                                        ctypes.c_uint32, _vp, _vp, _vp]),
     "smcx_philox4x32_10": (None, [_P(ctypes.c_uint32), _P(ctypes.c_uint32), _P(ctypes.c_uint32)]),

@@ -1,7 +1,8 @@
 """Python handle over a batch of independent lattices (smcx_batch_* C ABI).
 
-PyTorch owns the device arena and the stream; admission, scheduling, the
-graph-captured sweep chunks and all computation run in libsmcx.so.
+PyTorch owns the device arena and the stream; admission, the work queue of
+the persistent sweep kernel, its online tuning, the graph-captured chunks and
+all computation run in libsmcx.so.
 """
 from __future__ import annotations
 
@@ -112,3 +113,32 @@ class Batch:
                                      ctypes.byref(lb)))
         return dict(active=int(a.value), free_slots=int(f.value), free_bytes=int(fb.value),
                     largest_free=int(lb.value))
+
+    # tuning (never changes results) ---------------------------------------
+    OPT_TILE, OPT_OCCUPANCY, OPT_SCHEDULE = 1, 2, 3
+
+    def set_option(self, key: int, value: int):
+        """key OPT_TILE (work-item shape index), OPT_SCHEDULE (0 persistent
+        queue, 1 one launch per colour phase) or OPT_OCCUPANCY (register
+        budget index); value -1 = tuned online."""
+        check(self.L.smcx_batch_set_option(self.h, int(key), int(value)))
+
+    def tuning(self):
+        t, sc, o, d = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32(), ctypes.c_uint32()
+        check(self.L.smcx_batch_tuning(self.h, ctypes.byref(t), ctypes.byref(sc), ctypes.byref(o),
+                                       ctypes.byref(d)))
+        return dict(tile=int(t.value), schedule=int(sc.value), occupancy=int(o.value),
+                    tuned=bool(d.value))
+
+    @staticmethod
+    def tile_shape(i: int):
+        c = (ctypes.c_uint32 * 3)()
+        check(_lib.lib().smcx_batch_tile_shape(int(i), c))
+        return tuple(int(v) for v in c)
+
+    def queue_stats(self):
+        """Items that waited for their job's previous phase, their polls and
+        the nanoseconds waited (summed over warps), since creation."""
+        out = (ctypes.c_uint64 * 3)()
+        check(self.L.smcx_batch_queue_stats(self.h, out))
+        return dict(waited_items=int(out[0]), polls=int(out[1]), wait_ns=int(out[2]))

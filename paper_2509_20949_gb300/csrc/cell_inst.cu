@@ -14,15 +14,6 @@ static cudaError_t single(const Geom& g, const PhaseArgs& a, const Tables& tab, 
   return cudaGetLastError();
 }
 
-template <int KIND, int M, int KMAX>
-static cudaError_t batch(const JobDev* jobs, const uint2* blocks, uint32_t n_blocks, uint32_t grid,
-                         uint32_t s, int colour, cudaStream_t st) {
-  using C = CCfg<KIND, M, KMAX>;
-  if (grid == 0) return cudaSuccess;
-  k_sweep_cells_batch<C><<<grid, C::NT, 0, st>>>(jobs, blocks, n_blocks, s, colour);
-  return cudaGetLastError();
-}
-
 }  // namespace cell
 
 // variant index = kind * 6 + (M - 2) * 2 + (K == 6)
@@ -61,15 +52,5 @@ cudaError_t launch_sweep_cells(const Geom& g, const PhaseArgs& a, const Tables& 
 #undef SMCX_SINGLE
 }
 
-cudaError_t launch_sweep_cells_batch(int variant, const void* jobs, const uint2* blocks,
-                                     uint32_t n_blocks, uint32_t grid, uint32_t s, int colour,
-                                     cudaStream_t st) {
-  const cell::JobDev* J = static_cast<const cell::JobDev*>(jobs);
-#define SMCX_BATCH(K, M, X) cell::batch<K, M, X>(J, blocks, n_blocks, grid, s, colour, st)
-  SMCX_CELL_SWITCH(SMCX_BATCH)
-#undef SMCX_BATCH
-}
-
-size_t cell_job_bytes() { return sizeof(cell::JobDev); }
 
 }  // namespace smcx

@@ -71,9 +71,16 @@ bool cell_supported(const Geom& g);
 int cell_variant(const Geom& g);
 cudaError_t launch_sweep_cells(const Geom& g, const PhaseArgs& a, const Tables& tab, uint8_t* occ,
                                const uint8_t* dtab, unsigned long long* stats, cudaStream_t st);
-// batched form: jobs = device array of cell::JobDev, blocks = (job, first cell)
-cudaError_t launch_sweep_cells_batch(int variant, const void* jobs, const uint2* blocks,
-                                     uint32_t n_blocks, uint32_t grid, uint32_t s, int colour,
-                                     cudaStream_t st);
-size_t cell_job_bytes();
+// batched sweep (kernels_cell.cuh), args = cell::QueueArgs, one kernel pair
+// per register budget (3 or 4 resident blocks of 128 threads per SM):
+// launch_sweep_queue_N = the persistent schedule (a chunk of sweeps in one
+// launch; grid = n_sm x resident blocks per SM), launch_sweep_phase_N = one
+// colour phase ph of every job; sweep_queue_blocks_N() = resident blocks per
+// SM (0 on error)
+cudaError_t launch_sweep_queue_3(const void* args, int grid, cudaStream_t st);
+cudaError_t launch_sweep_queue_4(const void* args, int grid, cudaStream_t st);
+cudaError_t launch_sweep_phase_3(const void* args, uint32_t ph, cudaStream_t st);
+cudaError_t launch_sweep_phase_4(const void* args, uint32_t ph, cudaStream_t st);
+int sweep_queue_blocks_3();
+int sweep_queue_blocks_4();
 }  // namespace smcx

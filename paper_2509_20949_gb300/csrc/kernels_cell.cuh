@@ -30,9 +30,12 @@ namespace cell {
 using tiled::floordiv2;
 using tiled::round_up;
 
-template <int KIND_, int M_, int KMAX_>
+// INLINE_KEYS: the Philox key schedule is computed in registers (the batched
+// kernel, whose geometry sits in shared memory) instead of read from g.rk
+template <int KIND_, int M_, int KMAX_, bool INLINE_KEYS_ = false>
 struct CCfg {
   static constexpr int KIND = KIND_, M = M_, KMAX = KMAX_;
+  static constexpr bool INLINE_KEYS = INLINE_KEYS_;
   static constexpr int NB = KIND == 0 ? 2 : 4;
   static constexpr int W = KMAX <= 5 ? 6 : 5;
   static constexpr int Z1 = shell_z(KIND, 0);
@@ -153,6 +156,7 @@ __device__ __forceinline__ void run_cell(const Geom& g, uint8_t* __restrict__ oc
     hi[d] = link_bound(g, d, c[d] + 1);
   }
   const uint32_t cid = (static_cast<uint32_t>(cz) * g.m[1] + cy) * g.m[0] + cx;
+  const uint32_t key0 = g.seed_lo, key1 = g.seed_hi;
   const int nx = g.n[0], ny = g.n[1], nz = g.n[2];
   const uint32_t px = static_cast<uint32_t>(g.px);
   const uint32_t zstr = px * static_cast<uint32_t>(ny);
@@ -268,11 +272,15 @@ __device__ __forceinline__ void run_cell(const Geom& g, uint8_t* __restrict__ oc
           }
         };
 
-        const U4 w0 = philox4x32_10_rk(cc * (C::NB / 2), cid, t, 0u, g.rk);
+        auto draw = [&](uint32_t c0) {
+          if constexpr (C::INLINE_KEYS) return philox4x32_10(c0, cid, t, 0u, key0, key1);
+          else return philox4x32_10_rk(c0, cid, t, 0u, g.rk);
+        };
+        const U4 w0 = draw(cc * (C::NB / 2));
         attempt(std::integral_constant<int, 0>{}, w0.x, w0.y);
         attempt(std::integral_constant<int, 1>{}, w0.z, w0.w);
         if constexpr (C::NB == 4) {
-          const U4 w1 = philox4x32_10_rk(cc * 2 + 1, cid, t, 0u, g.rk);
+          const U4 w1 = draw(cc * 2 + 1);
           attempt(std::integral_constant<int, 2>{}, w1.x, w1.y);
           attempt(std::integral_constant<int, 3>{}, w1.z, w1.w);
         }
@@ -343,6 +351,8 @@ __global__ void __launch_bounds__(C::NT, 4) k_sweep_cells_single(const __grid_co
   warp_reduce_add_stats(stats, n_att, n_unl, n_acc, sum_de);
 }
 
+// ---- batched form: one persistent launch runs a chunk of sweeps of every job
+
 // one job of a batch, as the batched kernel reads it
 struct JobDev {
   Geom g;
@@ -354,37 +364,287 @@ struct JobDev {
   uint32_t sweeps;              // sweeps the job runs in this chunk
   int mode, sbin;               // acceptance mode and bin shift of its temperature
   int no_shift;                 // SMCX_NO_SHIFT
-  int pad_;
+  int variant;                  // cell_variant(g)
+  uint32_t items;               // work items of one colour phase
+  uint32_t ex, ey;              // items along x and y of the active-cell grid
+  uint32_t A[3];                // active cells of a colour along each axis
 };
 
-// One colour phase of sweep s of the chunk for every job of one kernel
-// variant: blocks[i] = (job, first cell index) of block i.
-template <class C>
-__global__ void __launch_bounds__(C::NT, 4) k_sweep_cells_batch(const JobDev* __restrict__ jobs,
-                                                             const uint2* __restrict__ blocks,
-                                                             uint32_t n_blocks, uint32_t s,
-                                                             int colour) {
-  __shared__ __align__(16) uint8_t smem[C::SMEM];
-  __shared__ Geom sg;
-  if (blockIdx.x >= n_blocks) return;
-  const uint2 bk = blocks[blockIdx.x];
-  const JobDev* J = jobs + bk.x;
-  if (threadIdx.x == 0) sg = J->g;
-  load_tables<C>(smem, J->tab, J->dtab);
+// The chunk's work queue.  Item i is item k = i mod n_items of colour phase
+// ph = i / n_items (sweep ph / 8, colour ph mod 8); within a phase the items
+// of the active jobs follow one another in `order`.  An item is 32 active
+// cells of one job, one per lane of a warp: with tx < 0 the next 32 cells of
+// the colour in x-fastest order, else a box of 2^tx x 2^ty x 2^(5-tx-ty)
+// cells of the colour's active-cell grid.
+struct QueueArgs {
+  const JobDev* jobs;
+  const uint32_t* order;        // slots of the active jobs
+  const uint32_t* first;        // first item of order[a] within a phase; first[n_active] = n_items
+  uint32_t n_active;
+  uint32_t n_items;
+  unsigned long long n_total;   // n_items * 8 * (sweeps of the chunk)
+  unsigned long long* ctr;      // [0] queue head, [1] status, [2 + slot] items finished per job
+  unsigned long long* qstats;   // [0] items that waited, [1] polls, [2] ns waited
+  int tx, ty;
+};
+
+constexpr unsigned long long kQueueTimeout = 1;        // status: a wait gave up
+constexpr unsigned long long kWaitLimitNs = 2000000000ull;  // 2 s per wait
+constexpr uint32_t kWaitMaxPolls = 1u << 24;                // and at most this many polls
+// per-warp shared tables of the batched kernel: thresholds, then the largest
+// difference table (K = 6, M = 4)
+constexpr int kQueueDBytes = 6 * 6 * 160;
+constexpr int kQueueWarpBytes = 4 * kTabWords + kQueueDBytes;
+constexpr int kQueueWarps = 4;
+constexpr int kQueueSmem = kQueueWarps * kQueueWarpBytes;  // dynamic shared memory per block
+
+__device__ __forceinline__ unsigned long long globaltimer_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ unsigned long long ld_relaxed(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+
+// Bounded wait until *p >= need (relaxed polls with exponential back-off,
+// 32 ns to 4 us, so that waiting warps do not crowd the L2 slice of the
+// counter; the caller fences after a success).  False when the status word
+// is set by another warp, after kWaitLimitNs, or after kWaitMaxPolls polls.
+// A wait that polled adds itself, its polls and its duration to qstats.
+static __device__ __noinline__ bool wait_at_least(const unsigned long long* p,
+                                                  unsigned long long need,
+                                                  const unsigned long long* status,
+                                                  unsigned long long* qstats) {
+  if (ld_relaxed(p) >= need) return true;
+  const unsigned long long t0 = globaltimer_ns();
+  uint32_t sleep_ns = 32;
+  bool ok = false;
+  uint32_t it = 1;
+  for (; it <= kWaitMaxPolls; ++it) {
+    __nanosleep(sleep_ns);
+    if (sleep_ns < 4096) sleep_ns <<= 1;
+    if (ld_relaxed(p) >= need) {
+      ok = true;
+      break;
+    }
+    if ((it & 15u) == 0) {
+      if (ld_relaxed(status) != 0) break;
+      if (globaltimer_ns() - t0 > kWaitLimitNs) break;
+    }
+  }
+  atomicAdd(qstats, 1ull);
+  atomicAdd(qstats + 1, static_cast<unsigned long long>(it));
+  atomicAdd(qstats + 2, globaltimer_ns() - t0);
+  return ok;
+}
+
+template <int KIND, int M, int KMAX>
+__device__ __forceinline__ void run_queued(const Geom& g, uint8_t* occ, int mode, int sbin,
+                                           uint32_t t, const int* shift, const int* c,
+                                           const uint32_t* s_tab, const uint8_t* s_d,
+                                           const int* s_pt, uint32_t* n_att, uint32_t* n_unl,
+                                           uint32_t* n_acc, int64_t* sum_de) {
+  using C = CCfg<KIND, M, KMAX, true>;
+  run_cell<C>(g, occ, t, shift, c[0], c[1], c[2], mode, sbin, s_tab, s_d,
+              s_pt + (KIND ? 2 * shell_z(0, 0) : 0), n_att, n_unl, n_acc, sum_de);
+}
+
+// Shared state of a block of either batched schedule: the partner tables of
+// both lattice kinds and each warp's copy of its current job's geometry
+// (its tables sit in the warp's slice of the dynamic shared memory).
+struct QueueShared {
+  int pt[2 * shell_z(0, 0) + 4 * shell_z(1, 0)];
+  Geom g[kQueueWarps];
+};
+
+__device__ __forceinline__ void queue_block_init(QueueShared& sh) {
+  constexpr int kPtB = 2 * shell_z(0, 0), kPtF = 4 * shell_z(1, 0);
+  if (threadIdx.x == 0) {
+    fill_cpartner<CCfg<0, 2, 5>>(sh.pt, std::make_integer_sequence<int, kPtB>{});
+    fill_cpartner<CCfg<1, 2, 5>>(sh.pt + kPtB, std::make_integer_sequence<int, kPtF>{});
+  }
   __syncthreads();
+}
+
+// job slot of item k of a phase and the item's index within the job
+__device__ __forceinline__ uint32_t queue_job(const QueueArgs& q, uint32_t k, uint32_t* li) {
+  uint32_t lo = 0, hi = q.n_active;  // first[lo] <= k < first[hi]
+  while (hi - lo > 1) {
+    const uint32_t mid = (lo + hi) >> 1;
+    if (__ldg(q.first + mid) <= k) lo = mid;
+    else hi = mid;
+  }
+  *li = k - __ldg(q.first + lo);
+  return __ldg(q.order + lo);
+}
+
+// the job's geometry and tables into the warp's shared slot, unless the
+// warp's previous item was of the same job (warp-uniform)
+__device__ __forceinline__ void queue_load_job(const JobDev* J, uint32_t slot, uint32_t* cur,
+                                               Geom* g, uint8_t* w_smem, int lane) {
+  if (slot == *cur) return;
+  const uint32_t* gsrc = reinterpret_cast<const uint32_t*>(&J->g);
+  uint32_t* gdst = reinterpret_cast<uint32_t*>(g);
+  for (int w = lane; w < static_cast<int>(sizeof(Geom) / 4); w += 32) gdst[w] = __ldg(gsrc + w);
+  const uint4* tsrc = reinterpret_cast<const uint4*>(
+      __ldg(reinterpret_cast<const unsigned long long*>(&J->tab)));
+  const uint4* dsrc = reinterpret_cast<const uint4*>(
+      __ldg(reinterpret_cast<const unsigned long long*>(&J->dtab)));
+  uint4* tdst = reinterpret_cast<uint4*>(w_smem);
+  for (int w = lane; w < kTabWords / 4; w += 32) tdst[w] = __ldg(tsrc + w);
+  uint4* ddst = reinterpret_cast<uint4*>(w_smem + 4 * kTabWords);
+  for (int w = lane; w < kQueueDBytes / 16; w += 32) ddst[w] = __ldg(dsrc + w);
+  *cur = slot;
+  __syncwarp();
+}
+
+// The 32 cells of item li of colour phase ph (sweep ph / 8 of the chunk) of
+// job J, one per lane, then the warp's statistics into the job's counters.
+__device__ __forceinline__ void queue_run_item(const QueueArgs& q, const JobDev* J, uint32_t ph,
+                                               uint32_t li, int lane, const Geom& g,
+                                               const uint8_t* w_smem, const int* s_pt) {
+  const uint32_t* const s_tab = reinterpret_cast<const uint32_t*>(w_smem);
+  const uint8_t* const s_d = w_smem + 4 * kTabWords;
+  const int colour = static_cast<int>(ph & 7u);
+  const uint32_t A0 = __ldg(&J->A[0]), A1 = __ldg(&J->A[1]);
+  uint32_t a[3];
+  if (q.tx < 0) {
+    const uint32_t ci = li * 32u + static_cast<uint32_t>(lane);
+    a[0] = ci % A0;
+    a[1] = (ci / A0) % A1;
+    a[2] = ci / (A0 * A1);
+  } else {
+    const int tz = 5 - q.tx - q.ty;
+    const uint32_t ex = __ldg(&J->ex), ey = __ldg(&J->ey);
+    const uint32_t ix = li % ex, r = li / ex;
+    const uint32_t iy = r % ey, iz = r / ey;
+    a[0] = (ix << q.tx) + (lane & ((1u << q.tx) - 1u));
+    a[1] = (iy << q.ty) + ((lane >> q.tx) & ((1u << q.ty) - 1u));
+    a[2] = (iz << tz) + (static_cast<uint32_t>(lane) >> (q.tx + q.ty));
+  }
+  bool active = true;
+  int c[3];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    const int bit = (colour >> d) & 1;
+    active = active && a[d] < __ldg(&J->A[d]) && !(g.m[d] == 1 && bit);
+    c[d] = g.m[d] == 1 ? 0 : static_cast<int>(2 * a[d]) + bit;
+  }
   uint32_t n_att = 0, n_unl = 0, n_acc = 0;
   int64_t sum_de = 0;
-  if (s < J->sweeps) {
-    const uint32_t t = J->t0 + s;
+  if (active) {
+    const uint32_t t = __ldg(&J->t0) + (ph >> 3);
+    const int mode = __ldg(&J->mode), sbin = __ldg(&J->sbin);
+    uint8_t* const occ =
+        reinterpret_cast<uint8_t*>(__ldg(reinterpret_cast<const unsigned long long*>(&J->occ)));
     int shift[3];
-    sweep_shift(sg, t, J->no_shift != 0, shift);
-    int c[3];
-    if (colour_cell(sg, colour, bk.y + threadIdx.x, c))
-      run_cell<C>(sg, J->occ, t, shift, c[0], c[1], c[2], J->mode, J->sbin,
-                  reinterpret_cast<const uint32_t*>(smem), smem + C::D_OFF,
-                  reinterpret_cast<const int*>(smem + C::PT_OFF), &n_att, &n_unl, &n_acc, &sum_de);
+    sweep_shift(g, t, __ldg(&J->no_shift) != 0, shift);
+#define SMCX_RUNQ(KI, MM, KM)                                                                 \
+  run_queued<KI, MM, KM>(g, occ, mode, sbin, t, shift, c, s_tab, s_d, s_pt, &n_att, &n_unl, \
+                         &n_acc, &sum_de)
+    switch (__ldg(&J->variant)) {
+      case 0: SMCX_RUNQ(0, 2, 5); break;
+      case 1: SMCX_RUNQ(0, 2, 6); break;
+      case 2: SMCX_RUNQ(0, 3, 5); break;
+      case 3: SMCX_RUNQ(0, 3, 6); break;
+      case 4: SMCX_RUNQ(0, 4, 5); break;
+      case 5: SMCX_RUNQ(0, 4, 6); break;
+      case 6: SMCX_RUNQ(1, 2, 5); break;
+      case 7: SMCX_RUNQ(1, 2, 6); break;
+      case 8: SMCX_RUNQ(1, 3, 5); break;
+      case 9: SMCX_RUNQ(1, 3, 6); break;
+      case 10: SMCX_RUNQ(1, 4, 5); break;
+      default: SMCX_RUNQ(1, 4, 6); break;
+    }
+#undef SMCX_RUNQ
   }
-  warp_reduce_add_stats(J->stats, n_att, n_unl, n_acc, sum_de);
+  unsigned long long* const stats = reinterpret_cast<unsigned long long*>(
+      __ldg(reinterpret_cast<const unsigned long long*>(&J->stats)));
+  warp_reduce_add_stats(stats, n_att, n_unl, n_acc, sum_de);
+}
+
+// Persistent schedule: every colour phase of a chunk of sweeps of every job
+// of a batch in one launch.  Warps take items from the queue in order;
+// before it starts an item of phase ph of a job, a warp waits (bounded)
+// until all items of the job's phases before ph have finished.  Items are
+// handed out in increasing order and a warp only waits for items handed out
+// before its own, all of them held by running warps, so the waits always
+// end.  A finished item is released (warp barrier, fence, counter
+// increment); the waiting lane polls the count with relaxed loads and fences
+// once it has seen it (acquire), then the warp barrier passes that on to the
+// other lanes.
+template <int MINB>
+__global__ void __launch_bounds__(32 * kQueueWarps, MINB)
+    k_sweep_cells_queue(const __grid_constant__ QueueArgs q) {
+  extern __shared__ __align__(16) uint8_t q_smem[];
+  __shared__ QueueShared sh;
+  queue_block_init(sh);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  uint8_t* const w_smem = q_smem + warp * kQueueWarpBytes;
+  unsigned long long* const head = q.ctr;
+  unsigned long long* const status = q.ctr + 1;
+  unsigned long long* const done = q.ctr + 2;
+  uint32_t cur = 0xFFFFFFFFu;
+  for (;;) {
+    unsigned long long i = 0;
+    int stop = 0;
+    if (lane == 0) {
+      stop = ld_relaxed(status) != 0;
+      if (!stop) i = atomicAdd(head, 1ull);
+    }
+    stop = __shfl_sync(0xffffffffu, stop, 0);
+    i = __shfl_sync(0xffffffffu, i, 0);
+    if (stop || i >= q.n_total) break;
+    const uint32_t ph = static_cast<uint32_t>(i / q.n_items);
+    const uint32_t k = static_cast<uint32_t>(i - static_cast<unsigned long long>(ph) * q.n_items);
+    uint32_t li;
+    const uint32_t slot = queue_job(q, k, &li);
+    const JobDev* J = q.jobs + slot;
+    if ((ph >> 3) >= __ldg(&J->sweeps)) continue;  // the job stops earlier; nobody waits for it
+    queue_load_job(J, slot, &cur, &sh.g[warp], w_smem, lane);
+    int ok = 1;
+    if (lane == 0 && ph != 0) {
+      ok = wait_at_least(done + slot, static_cast<unsigned long long>(ph) * __ldg(&J->items), status,
+                         q.qstats);
+      if (ok) __threadfence();
+      else atomicExch(status, kQueueTimeout);
+    }
+    ok = __shfl_sync(0xffffffffu, ok, 0);
+    if (!ok) break;
+    __syncwarp();
+    queue_run_item(q, J, ph, li, lane, sh.g[warp], w_smem, sh.pt);
+    __syncwarp();
+    if (lane == 0) {
+      __threadfence();
+      atomicAdd(done + slot, 1ull);
+    }
+  }
+}
+
+// Phase-synchronous schedule: colour phase ph of every job of a batch in
+// one launch (kernel boundaries order the phases); warp w of block b runs
+// item 4b + w of the phase.
+template <int MINB>
+__global__ void __launch_bounds__(32 * kQueueWarps, MINB)
+    k_sweep_cells_phase(const __grid_constant__ QueueArgs q, uint32_t ph) {
+  extern __shared__ __align__(16) uint8_t q_smem[];
+  __shared__ QueueShared sh;
+  queue_block_init(sh);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const uint32_t k = blockIdx.x * kQueueWarps + warp;
+  if (k >= q.n_items) return;
+  uint8_t* const w_smem = q_smem + warp * kQueueWarpBytes;
+  uint32_t li;
+  const uint32_t slot = queue_job(q, k, &li);
+  const JobDev* J = q.jobs + slot;
+  if ((ph >> 3) >= __ldg(&J->sweeps)) return;
+  uint32_t cur = 0xFFFFFFFFu;
+  queue_load_job(J, slot, &cur, &sh.g[warp], w_smem, lane);
+  queue_run_item(q, J, ph, li, lane, sh.g[warp], w_smem, sh.pt);
 }
 
 }  // namespace cell

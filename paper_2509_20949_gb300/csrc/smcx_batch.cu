@@ -4,13 +4,23 @@
 //
 // The caller hands over one device arena.  Its head holds the control area
 // (device job table, threshold and difference tables per job slot, per-job
-// statistics, block tables, a transfer buffer); the rest is a job heap from
-// which every admitted lattice gets its occupancy (first-fit, coalescing free
-// list).  A chunk of S sweeps runs every active job: per sweep and colour one
-// launch per kernel variant covers all jobs of that variant, blocks mapped to
-// (job, first cell); jobs with fewer sweeps left simply stop.  With a stream
-// the 8 * S * variants launches are captured once into a CUDA graph and
-// replayed until the job set changes.
+// statistics, the work-item order and queue counters, a transfer buffer);
+// the rest is a job heap from which every admitted lattice gets its
+// occupancy (first-fit, coalescing free list).  Work items are 32 active
+// link cells of one job and colour phase (kernels_cell.cuh), ordered within
+// a phase with the jobs whose largest cells have the most trials first.  Two
+// schedules run a chunk of S sweeps of every active job: the persistent
+// queue (one launch; warps take items in phase order, a per-job counter of
+// finished items keeps each job's phases in sequence), or one launch per
+// colour phase for all jobs.  With a stream the chunk is captured into a
+// CUDA graph, replayed until the job set or the tuning changes.
+//
+// Tuning (results never depend on it): item shape, schedule and register
+// budget are picked online.  While untuned, a run spends its first sweeps on
+// short sub-chunks, one per candidate, each timed with CUDA events
+// (attempted swaps per millisecond), and keeps the fastest; splitting a
+// chunk into sub-chunks does not change any job's trajectory.  Tuning
+// restarts when the number of items per phase has moved by more than 2x.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -40,7 +50,25 @@ namespace {
 constexpr size_t kAlign = 256;
 constexpr size_t kTabBytes = 4 * kTabWords;
 constexpr size_t kDtabBytes = 6 * 6 * 160;  // largest difference table (K = 6, M = 4)
-constexpr int kVariants = 12;
+
+// work items of 32 active cells: {-1, 0} = the next 32 cells of the colour in
+// x-fastest order (rows wrap), else boxes (log2 x, log2 y), z = 5 - x - y
+constexpr int kTiles[][2] = {{-1, 0}, {3, 2}, {2, 2}, {1, 2}};
+constexpr int kTileCount = 4;
+// register budgets: 3 or 4 resident blocks of 128 threads per SM
+constexpr int kOccCount = 2;
+// schedules: 0 = persistent work queue (one launch per chunk), 1 = one
+// launch per colour phase
+constexpr int kSchedCount = 2;
+constexpr int kDefaultTile = 0, kDefaultSched = 1, kDefaultOcc = 1;
+constexpr uint32_t kTuneSweeps = 2;  // sweeps per timed candidate
+
+using QueueLauncher = cudaError_t (*)(const void*, int, cudaStream_t);
+constexpr QueueLauncher kLaunchers[] = {launch_sweep_queue_3, launch_sweep_queue_4};
+using PhaseLauncher = cudaError_t (*)(const void*, uint32_t, cudaStream_t);
+constexpr PhaseLauncher kPhaseLaunchers[] = {launch_sweep_phase_3, launch_sweep_phase_4};
+using QueueBlocks = int (*)();
+constexpr QueueBlocks kBlocks[] = {sweep_queue_blocks_3, sweep_queue_blocks_4};
 
 size_t aup(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
@@ -106,30 +134,35 @@ struct Job {
   uint32_t total = 0, done_sweeps = 0, t = 0;
   int64_t E0 = 0;
   size_t occ_off = 0, occ_bytes = 0;
-  int variant = 0;
-  uint32_t cells = 0;  // active cells of a colour
+  uint64_t sites = 0;
+  uint32_t A[3] = {1, 1, 1};  // active cells of a colour per axis
   Geom g{};
   int mode = 0, sbin = 0;
 };
 
 struct ControlLayout {
-  size_t jobs, tabs, dtabs, stats, blocks, pairs, flag, scratch, heap;
-  uint32_t max_blocks;
+  size_t jobs, tabs, dtabs, stats, order, first, ctr, qstats, pairs, flag, scratch, heap;
 };
 
-ControlLayout control_layout(uint32_t max_jobs, size_t transfer_bytes, uint32_t max_blocks) {
+ControlLayout control_layout(uint32_t max_jobs, size_t transfer_bytes) {
   ControlLayout c;
   size_t o = 0;
   c.jobs = o;
-  o += aup(cell_job_bytes() * max_jobs, kAlign);
+  o += aup(sizeof(cell::JobDev) * max_jobs, kAlign);
   c.tabs = o;
   o += aup(kTabBytes * max_jobs, kAlign);
   c.dtabs = o;
   o += aup(kDtabBytes * max_jobs, kAlign);
   c.stats = o;
   o += aup(sizeof(unsigned long long) * 8 * max_jobs, kAlign);
-  c.blocks = o;
-  o += aup(sizeof(uint2) * max_blocks, kAlign);
+  c.order = o;
+  o += aup(sizeof(uint32_t) * max_jobs, kAlign);
+  c.first = o;
+  o += aup(sizeof(uint32_t) * (max_jobs + 1), kAlign);
+  c.ctr = o;
+  o += aup(sizeof(unsigned long long) * (2 + max_jobs), kAlign);
+  c.qstats = o;
+  o += aup(sizeof(unsigned long long) * 4, kAlign);
   c.pairs = o;
   o += aup(sizeof(unsigned long long) * 4 * 6 * 6, kAlign);
   c.flag = o;
@@ -137,11 +170,78 @@ ControlLayout control_layout(uint32_t max_jobs, size_t transfer_bytes, uint32_t 
   c.scratch = o;
   o += aup(transfer_bytes, kAlign);
   c.heap = o;
-  c.max_blocks = max_blocks;
   return c;
 }
 
-uint32_t blocks_for(uint32_t max_jobs) { return std::max<uint32_t>(1u << 16, max_jobs * 64u); }
+uint32_t ceil_shift(uint32_t a, int s) { return (a + (1u << s) - 1) >> s; }
+
+// items of one colour phase of a job for tile index `tile`
+uint32_t job_items(const Job& j, int tile, uint32_t* ex, uint32_t* ey) {
+  if (kTiles[tile][0] < 0) {
+    if (ex) *ex = 0;
+    if (ey) *ey = 0;
+    return (j.A[0] * j.A[1] * j.A[2] + 31) / 32;
+  }
+  const int tx = kTiles[tile][0], ty = kTiles[tile][1], tz = 5 - tx - ty;
+  const uint32_t x = ceil_shift(j.A[0], tx), y = ceil_shift(j.A[1], ty), z = ceil_shift(j.A[2], tz);
+  if (ex) *ex = x;
+  if (ey) *ey = y;
+  return x * y * z;
+}
+
+// Online choice of (tile, schedule, register budget) by coordinate descent:
+// every value of one knob with the others at their best so far, knob after
+// knob, each configuration measured once; forced knobs are not searched.
+struct Tuner {
+  static constexpr int kDims = 3;
+  static constexpr int kCount[kDims] = {kTileCount, kSchedCount, kOccCount};
+  static constexpr int kDefault[kDims] = {kDefaultTile, kDefaultSched, kDefaultOcc};
+  int forced[kDims] = {-1, -1, -1};
+  int cand[kDims] = {kDefaultTile, kDefaultSched, kDefaultOcc};
+  int best[kDims] = {kDefaultTile, kDefaultSched, kDefaultOcc};
+  double best_rate = 0;
+  bool tuned = false;
+  int dim = 0, idx = 0;
+  std::map<int, double> seen;  // measured configurations -> attempted swaps per ms
+  uint32_t tuned_items = 0;
+
+  int tile() const { return cand[0]; }
+  int sched() const { return cand[1]; }
+  int occ() const { return cand[2]; }
+  static int enc(const int* c) { return (c[0] * 4 + c[1]) * 4 + c[2]; }
+
+  void restart() {
+    for (int d = 0; d < kDims; ++d) best[d] = forced[d] >= 0 ? forced[d] : kDefault[d];
+    best_rate = 0;
+    seen.clear();
+    tuned = false;
+    dim = idx = 0;
+    advance();
+  }
+  // next configuration to measure, or the best one once all are measured
+  void advance() {
+    for (; dim < kDims; ++dim, idx = 0) {
+      if (forced[dim] >= 0) continue;
+      for (; idx < kCount[dim]; ++idx) {
+        int c[kDims] = {best[0], best[1], best[2]};
+        c[dim] = idx;
+        if (seen.count(enc(c))) continue;
+        for (int d = 0; d < kDims; ++d) cand[d] = c[d];
+        return;
+      }
+    }
+    for (int d = 0; d < kDims; ++d) cand[d] = best[d];
+    tuned = true;
+  }
+  void record(double rate) {
+    seen[enc(cand)] = rate;
+    if (rate > best_rate) {
+      best_rate = rate;
+      for (int d = 0; d < kDims; ++d) best[d] = cand[d];
+    }
+    advance();
+  }
+};
 
 }  // namespace
 
@@ -155,17 +255,24 @@ struct smcx_batch {
   Heap heap;
   std::vector<Job> jobs;
   std::vector<uint32_t> done_queue;
-  bool dirty = true;
+  bool dirty = true;  // the job set changed: rebuild the queue order
   int n_sm = 0;
+  int grid[kOccCount] = {};  // persistent grid of each register budget
   smcx_status sticky = SMCX_OK;
-  // block tables per variant (offset into the device block array, count)
-  uint32_t var_off[kVariants] = {}, var_cnt[kVariants] = {};
+  std::vector<uint32_t> order;  // active slots (queue order)
+  int queue_tile = -1;          // tile the device order/first arrays were built for
+  uint32_t n_items = 0;         // items of one phase over all active jobs
+  Tuner tuner;
+  cudaEvent_t ev[2] = {nullptr, nullptr};
   cudaGraphExec_t graph = nullptr;
-  uint32_t graph_chunk = 0;
+  uint32_t graph_sweeps = 0;
+  int graph_tile = -1, graph_sched = -1, graph_occ = -1;
 
   uint8_t* at(size_t off) { return arena + off; }
   uint8_t* scratch() { return at(cl.scratch); }
   unsigned int* flag() { return reinterpret_cast<unsigned int*>(at(cl.flag)); }
+  unsigned long long* ctr() { return reinterpret_cast<unsigned long long*>(at(cl.ctr)); }
+  unsigned long long* qstats() { return reinterpret_cast<unsigned long long*>(at(cl.qstats)); }
   unsigned long long* stats(uint32_t slot) {
     return reinterpret_cast<unsigned long long*>(at(cl.stats)) + 8 * slot;
   }
@@ -193,39 +300,171 @@ smcx_status bcheck(smcx_batch* b) {
 void drop_graph(smcx_batch* b) {
   if (b->graph) cudaGraphExecDestroy(b->graph);
   b->graph = nullptr;
-  b->graph_chunk = 0;
+  b->graph_sweeps = 0;
+  b->graph_tile = b->graph_sched = b->graph_occ = -1;
 }
 
-// rebuild the per-variant block tables of the active jobs
-smcx_status rebuild_blocks(smcx_batch* b) {
-  std::vector<uint2> all;
-  for (int v = 0; v < kVariants; ++v) {
-    b->var_off[v] = static_cast<uint32_t>(all.size());
-    for (uint32_t slot = 0; slot < b->max_jobs; ++slot) {
-      const Job& j = b->jobs[slot];
-      if (!j.used || j.done || j.variant != v) continue;
-      for (uint32_t c0 = 0; c0 < j.cells; c0 += 128) all.push_back(make_uint2(slot, c0));
-    }
-    b->var_cnt[v] = static_cast<uint32_t>(all.size()) - b->var_off[v];
+// trials of the largest link cell of a job: the length of its chain of
+// dependent trials in one colour phase
+uint32_t longest_cell(const Job& j) {
+  uint32_t t = static_cast<uint32_t>(j.g.nb);
+  for (int d = 0; d < 3; ++d) t *= (j.desc.n[d] + j.g.m[d] - 1) / j.g.m[d];
+  return t;
+}
+
+// queue order and the first item of each job within a phase, for tile
+// `tile`: jobs with the longest chains of dependent trials first (their
+// phases bound the chunk), then the larger ones, then by slot
+smcx_status build_queue(smcx_batch* b, int tile) {
+  b->order.clear();
+  for (uint32_t slot = 0; slot < b->max_jobs; ++slot) {
+    const Job& j = b->jobs[slot];
+    if (j.used && !j.done) b->order.push_back(slot);
   }
-  if (all.size() > b->cl.max_blocks) return batch_fail(SMCX_EBUDGET, "block table full");
-  if (!all.empty())
-    BATCH_CUDA(b, cudaMemcpyAsync(b->at(b->cl.blocks), all.data(), sizeof(uint2) * all.size(),
+  std::stable_sort(b->order.begin(), b->order.end(), [&](uint32_t x, uint32_t y) {
+    const Job& a = b->jobs[x];
+    const Job& c = b->jobs[y];
+    const uint32_t la = longest_cell(a), lc = longest_cell(c);
+    if (la != lc) return la > lc;
+    return job_items(a, tile, nullptr, nullptr) > job_items(c, tile, nullptr, nullptr);
+  });
+  std::vector<uint32_t> first;
+  uint64_t n = 0;
+  for (uint32_t slot : b->order) {
+    first.push_back(static_cast<uint32_t>(n));
+    n += job_items(b->jobs[slot], tile, nullptr, nullptr);
+  }
+  first.push_back(static_cast<uint32_t>(n));
+  if (n >= (1ull << 31)) return batch_fail(SMCX_EBUDGET, "too many work items per phase");
+  b->n_items = static_cast<uint32_t>(n);
+  if (!b->order.empty()) {
+    BATCH_CUDA(b, cudaMemcpyAsync(b->at(b->cl.order), b->order.data(),
+                                  sizeof(uint32_t) * b->order.size(), cudaMemcpyHostToDevice,
+                                  b->stream));
+    BATCH_CUDA(b, cudaMemcpyAsync(b->at(b->cl.first), first.data(), sizeof(uint32_t) * first.size(),
                                   cudaMemcpyHostToDevice, b->stream));
-  drop_graph(b);
+  }
+  b->queue_tile = tile;
   b->dirty = false;
+  drop_graph(b);
   return SMCX_OK;
 }
 
-smcx_status enqueue_chunk(smcx_batch* b, uint32_t chunk) {
-  const uint2* blocks = reinterpret_cast<const uint2*>(b->at(b->cl.blocks));
-  for (uint32_t s = 0; s < chunk; ++s)
-    for (int colour = 0; colour < 8; ++colour)
-      for (int v = 0; v < kVariants; ++v) {
-        if (!b->var_cnt[v]) continue;
-        BATCH_CUDA(b, launch_sweep_cells_batch(v, b->at(b->cl.jobs), blocks + b->var_off[v],
-                                               b->var_cnt[v], b->var_cnt[v], s, colour, b->stream));
+// `sweeps` sweeps of every active job: counter reset + one launch of the
+// persistent kernel (sched 0), or one launch per colour phase (sched 1)
+smcx_status enqueue_chunk(smcx_batch* b, uint32_t sweeps, int tile, int sched, int occ) {
+  cell::QueueArgs q{};
+  q.jobs = reinterpret_cast<const cell::JobDev*>(b->at(b->cl.jobs));
+  q.order = reinterpret_cast<const uint32_t*>(b->at(b->cl.order));
+  q.first = reinterpret_cast<const uint32_t*>(b->at(b->cl.first));
+  q.n_active = static_cast<uint32_t>(b->order.size());
+  q.n_items = b->n_items;
+  q.n_total = static_cast<unsigned long long>(b->n_items) * 8ull * sweeps;
+  q.ctr = b->ctr();
+  q.qstats = b->qstats();
+  q.tx = kTiles[tile][0];
+  q.ty = kTiles[tile][1];
+  if (sched == 0) {
+    BATCH_CUDA(b, cudaMemsetAsync(b->ctr(), 0, sizeof(unsigned long long) * (2 + b->max_jobs),
+                                  b->stream));
+    BATCH_CUDA(b, kLaunchers[occ](&q, b->grid[occ], b->stream));
+  } else {
+    for (uint32_t ph = 0; ph < 8 * sweeps; ++ph)
+      BATCH_CUDA(b, kPhaseLaunchers[occ](&q, ph, b->stream));
+  }
+  return SMCX_OK;
+}
+
+// Runs `sweeps` sweeps of every active job with (tile, sched, occ);
+// graph-captured when `use_graph` and a stream is bound.  *trials =
+// attempted swaps, *ms = device time (when ms != NULL, timed with events).
+smcx_status run_sweeps(smcx_batch* b, uint32_t sweeps, int tile, int sched, int occ,
+                       bool use_graph, uint32_t* n_finished, uint64_t* trials, float* ms) {
+  smcx_status s;
+  if (b->dirty || b->queue_tile != tile) {
+    s = build_queue(b, tile);
+    if (s != SMCX_OK) return s;
+  }
+  std::vector<uint8_t> table(sizeof(cell::JobDev) * b->max_jobs, 0);
+  uint32_t s_max = 0;
+  uint64_t tr = 0;
+  for (uint32_t slot : b->order) {
+    const Job& j = b->jobs[slot];
+    cell::JobDev jd{};
+    jd.g = j.g;
+    jd.occ = b->at(j.occ_off);
+    jd.dtab = b->at(b->cl.dtabs) + kDtabBytes * slot;
+    jd.tab = reinterpret_cast<const uint32_t*>(b->at(b->cl.tabs) + kTabBytes * slot);
+    jd.stats = b->stats(slot);
+    jd.t0 = j.t;
+    jd.sweeps = std::min(sweeps, j.total - j.done_sweeps);
+    jd.mode = j.mode;
+    jd.sbin = j.sbin;
+    jd.no_shift = (j.desc.flags & SMCX_NO_SHIFT) ? 1 : 0;
+    jd.variant = cell_variant(j.g);
+    jd.items = job_items(j, tile, &jd.ex, &jd.ey);
+    for (int d = 0; d < 3; ++d) jd.A[d] = j.A[d];
+    std::memcpy(table.data() + sizeof(cell::JobDev) * slot, &jd, sizeof(jd));
+    s_max = std::max(s_max, jd.sweeps);
+    tr += j.sites * jd.sweeps;
+  }
+  if (n_finished) *n_finished = 0;
+  if (trials) *trials = tr;
+  if (ms) *ms = 0;
+  if (s_max == 0) return SMCX_OK;
+  BATCH_CUDA(b, cudaMemcpyAsync(b->at(b->cl.jobs), table.data(), table.size(),
+                                cudaMemcpyHostToDevice, b->stream));
+  if (ms) BATCH_CUDA(b, cudaEventRecord(b->ev[0], b->stream));
+  if (use_graph && b->stream) {
+    if (!b->graph || b->graph_sweeps != s_max || b->graph_tile != tile || b->graph_sched != sched ||
+        b->graph_occ != occ) {
+      drop_graph(b);
+      cudaGraph_t gr = nullptr;
+      BATCH_CUDA(b, cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
+      s = enqueue_chunk(b, s_max, tile, sched, occ);
+      cudaError_t e = cudaStreamEndCapture(b->stream, &gr);
+      if (s != SMCX_OK) {
+        if (gr) cudaGraphDestroy(gr);
+        return s;
       }
+      if (e != cudaSuccess) return bcuda(b, e, "graph capture");
+      e = cudaGraphInstantiate(&b->graph, gr, 0);
+      cudaGraphDestroy(gr);
+      if (e != cudaSuccess) return bcuda(b, e, "graph instantiate");
+      b->graph_sweeps = s_max;
+      b->graph_tile = tile;
+      b->graph_sched = sched;
+      b->graph_occ = occ;
+    }
+    BATCH_CUDA(b, cudaGraphLaunch(b->graph, b->stream));
+  } else {
+    s = enqueue_chunk(b, s_max, tile, sched, occ);
+    if (s != SMCX_OK) return s;
+  }
+  if (ms) BATCH_CUDA(b, cudaEventRecord(b->ev[1], b->stream));
+  unsigned long long status = 0;
+  BATCH_CUDA(b, cudaMemcpyAsync(&status, b->ctr() + 1, sizeof(status), cudaMemcpyDeviceToHost,
+                                b->stream));
+  BATCH_CUDA(b, cudaStreamSynchronize(b->stream));
+  if (status != 0) {
+    b->sticky = SMCX_ETIMEOUT;
+    return batch_fail(SMCX_ETIMEOUT, "batched sweep: a wait for a job's previous phase gave up");
+  }
+  if (ms) BATCH_CUDA(b, cudaEventElapsedTime(ms, b->ev[0], b->ev[1]));
+  uint32_t fin = 0;
+  for (uint32_t slot : b->order) {
+    Job& j = b->jobs[slot];
+    const uint32_t ran = std::min(sweeps, j.total - j.done_sweeps);
+    j.done_sweeps += ran;
+    j.t += ran;
+    if (j.done_sweeps == j.total) {
+      j.done = true;
+      b->done_queue.push_back(slot);
+      b->dirty = true;
+      ++fin;
+    }
+  }
+  if (n_finished) *n_finished = fin;
   return SMCX_OK;
 }
 
@@ -262,7 +501,7 @@ extern "C" {
 
 size_t smcx_batch_control_bytes(uint32_t max_jobs, size_t transfer_bytes) {
   if (max_jobs == 0) return 0;
-  return control_layout(max_jobs, transfer_bytes, blocks_for(max_jobs)).heap;
+  return control_layout(max_jobs, transfer_bytes).heap;
 }
 
 size_t smcx_batch_job_bytes(const smcx_lattice_desc* desc) {
@@ -278,7 +517,7 @@ smcx_status smcx_batch_create(uint32_t max_jobs, void* d_arena, size_t arena_byt
   if (max_jobs == 0 || !d_arena) return batch_fail(SMCX_EINVAL, "max_jobs and arena required");
   if (reinterpret_cast<uintptr_t>(d_arena) % kAlign)
     return batch_fail(SMCX_EINVAL, "arena must be 256-byte aligned");
-  const ControlLayout cl = control_layout(max_jobs, transfer_bytes, blocks_for(max_jobs));
+  const ControlLayout cl = control_layout(max_jobs, transfer_bytes);
   if (arena_bytes < cl.heap) return batch_fail(SMCX_ENOMEM, "arena smaller than the control area");
   auto* b = new smcx_batch();
   b->arena = static_cast<uint8_t*>(d_arena);
@@ -289,13 +528,27 @@ smcx_status smcx_batch_create(uint32_t max_jobs, void* d_arena, size_t arena_byt
   b->cl = cl;
   b->heap.reset(arena_bytes - cl.heap);
   b->jobs.resize(max_jobs);
+  b->tuner.restart();
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&b->n_sm, cudaDevAttrMultiProcessorCount, dev);
   if (e == cudaSuccess)
     e = cudaMemsetAsync(b->at(cl.stats), 0, sizeof(unsigned long long) * 8 * max_jobs, b->stream);
+  if (e == cudaSuccess)
+    e = cudaMemsetAsync(b->at(cl.qstats), 0, sizeof(unsigned long long) * 4, b->stream);
+  if (e == cudaSuccess)  // queue head, status word and per-job counters
+    e = cudaMemsetAsync(b->at(cl.ctr), 0, sizeof(unsigned long long) * (2 + max_jobs), b->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+  for (int o = 0; o < kOccCount && e == cudaSuccess; ++o) {
+    const int per_sm = kBlocks[o]();
+    if (per_sm < 1) e = cudaErrorInvalidConfiguration;
+    b->grid[o] = b->n_sm * per_sm;
+  }
+  if (e == cudaSuccess) e = cudaEventCreate(&b->ev[0]);
+  if (e == cudaSuccess) e = cudaEventCreate(&b->ev[1]);
   if (e != cudaSuccess) {
+    for (cudaEvent_t ev : b->ev)
+      if (ev) cudaEventDestroy(ev);
     delete b;
     return batch_fail(SMCX_ECUDA, std::string("batch create: ") + cudaGetErrorString(e));
   }
@@ -351,9 +604,8 @@ smcx_status smcx_batch_add(smcx_batch* b, const smcx_lattice_desc* desc, const u
   int L = 0, m[3];
   host_layout(*desc, static_cast<int>(n_shells), &L, m);
   j.g = host_geom(*desc, static_cast<int>(n_shells), m);
-  j.variant = cell_variant(j.g);
-  j.cells = 1;
-  for (int d = 0; d < 3; ++d) j.cells *= m[d] == 1 ? 1u : static_cast<uint32_t>(m[d] / 2);
+  j.sites = N;
+  for (int d = 0; d < 3; ++d) j.A[d] = m[d] == 1 ? 1u : static_cast<uint32_t>(m[d] / 2);
   Tables tab;
   host_build_tables(T, &tab, &j.mode, &j.sbin);
   auto fail_release = [&](smcx_status st) {
@@ -400,72 +652,94 @@ smcx_status smcx_batch_run(smcx_batch* b, uint32_t chunk_sweeps, uint32_t* n_fin
   smcx_status s = bcheck(b);
   if (s != SMCX_OK) return s;
   if (chunk_sweeps == 0) return batch_fail(SMCX_EINVAL, "chunk_sweeps must be > 0");
-  if (b->dirty) {
-    s = rebuild_blocks(b);
-    if (s != SMCX_OK) return s;
-  }
-  // per-job chunk parameters
-  std::vector<uint8_t> table(cell_job_bytes() * b->max_jobs, 0);
-  bool any = false;
-  for (uint32_t slot = 0; slot < b->max_jobs; ++slot) {
-    Job& j = b->jobs[slot];
-    if (!j.used || j.done) continue;
-    cell::JobDev jd{};
-    jd.g = j.g;
-    jd.occ = b->at(j.occ_off);
-    jd.dtab = b->at(b->cl.dtabs) + kDtabBytes * slot;
-    jd.tab = reinterpret_cast<const uint32_t*>(b->at(b->cl.tabs) + kTabBytes * slot);
-    jd.stats = b->stats(slot);
-    jd.t0 = j.t;
-    jd.sweeps = std::min(chunk_sweeps, j.total - j.done_sweeps);
-    jd.mode = j.mode;
-    jd.sbin = j.sbin;
-    jd.no_shift = (j.desc.flags & SMCX_NO_SHIFT) ? 1 : 0;
-    std::memcpy(table.data() + cell_job_bytes() * slot, &jd, sizeof(jd));
-    any = true;
-  }
   if (n_finished) *n_finished = 0;
-  if (!any) return SMCX_OK;
-  BATCH_CUDA(b, cudaMemcpyAsync(b->at(b->cl.jobs), table.data(), table.size(),
-                                cudaMemcpyHostToDevice, b->stream));
-  if (b->stream) {
-    if (!b->graph || b->graph_chunk != chunk_sweeps) {
-      drop_graph(b);
-      cudaGraph_t gr = nullptr;
-      BATCH_CUDA(b, cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
-      s = enqueue_chunk(b, chunk_sweeps);
-      cudaError_t e = cudaStreamEndCapture(b->stream, &gr);
-      if (s != SMCX_OK) {
-        if (gr) cudaGraphDestroy(gr);
-        return s;
+  uint32_t left = chunk_sweeps;
+  while (left > 0) {
+    if (b->dirty) {
+      // re-tune when the work per phase has moved by more than 2x
+      uint64_t items = 0;
+      for (const Job& j : b->jobs)
+        if (j.used && !j.done) items += job_items(j, b->tuner.best[0], nullptr, nullptr);
+      const uint64_t ref = b->tuner.tuned_items;
+      if (b->tuner.tuned && items > 0 && (items > 2 * ref || 2 * items < ref)) b->tuner.restart();
+    }
+    uint32_t fin = 0;
+    if (!b->tuner.tuned) {
+      const uint32_t ts = std::min(left, kTuneSweeps);
+      uint64_t trials = 0;
+      float ms = 0;
+      s = run_sweeps(b, ts, b->tuner.tile(), b->tuner.sched(), b->tuner.occ(), false, &fin, &trials,
+                     &ms);
+      if (s != SMCX_OK) return s;
+      left -= ts;
+      if (trials == 0) break;  // no active job
+      b->tuner.record(ms > 0 ? static_cast<double>(trials) / ms : 0.0);
+      if (b->tuner.tuned) {
+        uint64_t items = 0;
+        for (const Job& j : b->jobs)
+          if (j.used && !j.done) items += job_items(j, b->tuner.tile(), nullptr, nullptr);
+        b->tuner.tuned_items = static_cast<uint32_t>(std::min<uint64_t>(items, 0xFFFFFFFFu));
       }
-      if (e != cudaSuccess) return bcuda(b, e, "graph capture");
-      e = cudaGraphInstantiate(&b->graph, gr, 0);
-      cudaGraphDestroy(gr);
-      if (e != cudaSuccess) return bcuda(b, e, "graph instantiate");
-      b->graph_chunk = chunk_sweeps;
+    } else {
+      uint64_t trials = 0;
+      s = run_sweeps(b, left, b->tuner.tile(), b->tuner.sched(), b->tuner.occ(), true, &fin, &trials,
+                     nullptr);
+      if (s != SMCX_OK) return s;
+      left = 0;
     }
-    BATCH_CUDA(b, cudaGraphLaunch(b->graph, b->stream));
-  } else {
-    s = enqueue_chunk(b, chunk_sweeps);
-    if (s != SMCX_OK) return s;
+    if (n_finished) *n_finished += fin;
   }
+  return SMCX_OK;
+}
+
+smcx_status smcx_batch_set_option(smcx_batch* b, uint32_t key, int64_t value) {
+  smcx_status s = bcheck(b);
+  if (s != SMCX_OK) return s;
+  int d = -1;
+  if (key == SMCX_BATCH_OPT_TILE) d = 0;
+  else if (key == SMCX_BATCH_OPT_SCHEDULE) d = 1;
+  else if (key == SMCX_BATCH_OPT_OCCUPANCY) d = 2;
+  if (d < 0) return batch_fail(SMCX_EINVAL, "unknown batch option");
+  if (value < -1 || value >= Tuner::kCount[d])
+    return batch_fail(SMCX_EINVAL, "batch option value out of range");
+  b->tuner.forced[d] = static_cast<int>(value);
+  b->tuner.restart();
+  return SMCX_OK;
+}
+
+smcx_status smcx_batch_tuning(smcx_batch* b, int32_t* tile, int32_t* schedule, int32_t* occupancy,
+                              uint32_t* tuned) {
+  if (!b) return batch_fail(SMCX_EINVAL, "null batch");
+  const bool t = b->tuner.tuned;
+  if (tile) *tile = t ? b->tuner.tile() : -1;
+  if (schedule) *schedule = t ? b->tuner.sched() : -1;
+  if (occupancy) *occupancy = t ? b->tuner.occ() : -1;
+  if (tuned) *tuned = t ? 1u : 0u;
+  return SMCX_OK;
+}
+
+smcx_status smcx_batch_queue_stats(smcx_batch* b, uint64_t* out) {
+  smcx_status s = bcheck(b);
+  if (s != SMCX_OK) return s;
+  if (!out) return batch_fail(SMCX_EINVAL, "null output");
+  unsigned long long h[3];
+  BATCH_CUDA(b, cudaMemcpyAsync(h, b->qstats(), sizeof(h), cudaMemcpyDeviceToHost, b->stream));
   BATCH_CUDA(b, cudaStreamSynchronize(b->stream));
-  uint32_t fin = 0;
-  for (uint32_t slot = 0; slot < b->max_jobs; ++slot) {
-    Job& j = b->jobs[slot];
-    if (!j.used || j.done) continue;
-    const uint32_t ran = std::min(chunk_sweeps, j.total - j.done_sweeps);
-    j.done_sweeps += ran;
-    j.t += ran;
-    if (j.done_sweeps == j.total) {
-      j.done = true;
-      b->done_queue.push_back(slot);
-      b->dirty = true;
-      ++fin;
-    }
+  for (int i = 0; i < 3; ++i) out[i] = h[i];
+  return SMCX_OK;
+}
+
+smcx_status smcx_batch_tile_shape(uint32_t i, uint32_t* cells_xyz) {
+  if (i >= static_cast<uint32_t>(kTileCount) || !cells_xyz)
+    return batch_fail(SMCX_EINVAL, "bad batch tile request");
+  if (kTiles[i][0] < 0) {  // 32 consecutive cells, x fastest
+    cells_xyz[0] = 32;
+    cells_xyz[1] = cells_xyz[2] = 1;
+    return SMCX_OK;
   }
-  if (n_finished) *n_finished = fin;
+  cells_xyz[0] = 1u << kTiles[i][0];
+  cells_xyz[1] = 1u << kTiles[i][1];
+  cells_xyz[2] = 1u << (5 - kTiles[i][0] - kTiles[i][1]);
   return SMCX_OK;
 }
 
@@ -537,6 +811,8 @@ smcx_status smcx_batch_info(smcx_batch* b, uint32_t* active, uint32_t* free_slot
 smcx_status smcx_batch_destroy(smcx_batch* b) {
   if (!b) return batch_fail(SMCX_EINVAL, "null batch");
   drop_graph(b);
+  for (cudaEvent_t ev : b->ev)
+    if (ev) cudaEventDestroy(ev);
   delete b;
   return SMCX_OK;
 }

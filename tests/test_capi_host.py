@@ -80,3 +80,19 @@ def test_buffer_sizes_and_validation(L):
     st = L.smcx_create_lattice(ctypes.byref(d), None, None, occ.ctypes.data, None, ctypes.byref(h))
     assert st == _lib.SMCX_EINVAL and not h.value
     assert b"null" in L.smcx_last_error()
+
+
+def test_batch_tile_shapes(L):
+    """The batched kernel's work-item boxes hold one warp of cells each."""
+    shapes = []
+    for i in range(4):
+        c = (ctypes.c_uint32 * 3)()
+        assert L.smcx_batch_tile_shape(i, c) == _lib.SMCX_OK
+        shapes.append(tuple(c))
+        assert np.prod(shapes[-1]) == 32 and all(v & (v - 1) == 0 for v in shapes[-1])
+    assert len(set(shapes)) == 4
+    c = (ctypes.c_uint32 * 3)()
+    assert L.smcx_batch_tile_shape(4, c) == _lib.SMCX_EINVAL
+    # options of a null batch are refused without a device
+    assert L.smcx_batch_set_option(None, 1, 0) == _lib.SMCX_EINVAL
+    assert L.smcx_batch_tuning(None, None, None, None, None) == _lib.SMCX_EINVAL

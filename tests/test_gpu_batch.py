@@ -109,3 +109,67 @@ def test_admission_budget():
     _add(b, case)
     with pytest.raises(SmcxError):
         b.add(0, (3, 4, 4), 3, np.zeros(96, np.uint8), inputs.epi_table(2, 3, 0.02, 0), 500.0, 1)
+
+
+def _mixed_jobs():
+    """Small jobs (one item per phase) next to larger ragged ones (many items
+    per phase), so that phases of one job span several warps."""
+    jobs = _jobs(3, 8, nmin=4, nmax=12)
+    for j, (kind, n, K, M) in enumerate([(1, (26, 22, 30), 5, 3), (0, (40, 37, 34), 6, 4),
+                                          (0, (33, 48, 20), 4, 2)]):
+        case = make_case(kind, n, K, M, seed=500 + j, sigma=0.03, epi_seed=600 + j, occ_seed=700 + j)
+        case.update(T=700.0 + 300.0 * j, sweeps=9 + j)
+        jobs.append(case)
+    return jobs
+
+
+def _run_all(b, jobs, chunk):
+    ids = [_add(b, c) for c in jobs]
+    done = set()
+    for _ in range(100):
+        b.run(chunk)
+        done |= set(b.poll())
+        if len(done) == len(jobs):
+            break
+    assert done == set(ids)
+    return [b.result(j) for j in ids]
+
+
+def test_every_tuning_choice_gives_the_same_bits():
+    """Work-item shape, schedule and register budget change only speed."""
+    require_cuda()
+    from paper_2509_20949_gb300.batch import Batch
+    jobs = _mixed_jobs()
+    alone = [_alone(c) for c in jobs]
+    for tile in range(4):
+        assert np.prod(Batch.tile_shape(tile)) == 32
+        for sched in range(2):
+            for occ in range(2):
+                b = _batch(max_jobs=16, arena=1 << 27)
+                b.set_option(Batch.OPT_TILE, tile)
+                b.set_option(Batch.OPT_SCHEDULE, sched)
+                b.set_option(Batch.OPT_OCCUPANCY, occ)
+                res = _run_all(b, jobs, 5)
+                assert b.tuning() == dict(tile=tile, schedule=sched, occupancy=occ, tuned=True)
+                for k, (r, (occ_a, st, E)) in enumerate(zip(res, alone)):
+                    assert np.array_equal(r["occ"], occ_a), (tile, sched, occ, k)
+                    assert r["stats"] == st and r["energy"] == E, (tile, sched, occ, k)
+                if sched == 1:
+                    assert b.queue_stats()["waited_items"] == 0  # no device-side waits
+                b.close()
+
+
+def test_online_tuning_converges_without_changing_results():
+    require_cuda()
+    jobs = _mixed_jobs()
+    for c in jobs:
+        c["sweeps"] = 30
+    b = _batch(max_jobs=16, arena=1 << 27)
+    assert b.tuning()["tuned"] is False
+    res = _run_all(b, jobs, 30)
+    t = b.tuning()
+    assert t["tuned"] and 0 <= t["tile"] < 4 and 0 <= t["schedule"] < 2 and 0 <= t["occupancy"] < 2
+    for k, (r, c) in enumerate(zip(res, jobs)):
+        occ_a, st, E = _alone(c)
+        assert np.array_equal(r["occ"], occ_a), k
+        assert r["stats"] == st and r["energy"] == E and r["sweeps"] == 30
