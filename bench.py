@@ -364,11 +364,18 @@ def main():
     def step(i):
         lat.sweep(1, sweep_temperature(w, i), stats=False)
 
-    # warm-up
+    # warm-up (also where the online kernel choice times its candidates)
     for i in range(args.warmup):
         step(i)
         lat.sro(M)
     torch.cuda.synchronize()
+    names = {1: "generic", 2: "tiled", 3: "cell"}
+    kt = lat.kernel_tuning()
+    kern, shape = lat.kernel_in_use()
+    kernel_choice = {"kernel": names.get(kern, str(kern)), "tile_shape": shape,
+                     "tuned": kt["done"],
+                     "candidates_ms": {f"{names.get(c['kernel'])}{'' if c['shape'] < 0 else c['shape']}":
+                                       round(c["best_ms"], 4) for c in kt["candidates"]}}
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
@@ -436,6 +443,7 @@ def main():
                          "frac": achieved / peak, "traffic": traffic,
                          "kernel": "sweep phase", "kernel_ms_per_launch": kernel_ms,
                          "peak_source": peak_src},
+            "kernel_choice": kernel_choice,
             "cpu_baseline": cpu,
             "clocks": clk,
             "gpu_launches": args.steps * (launches_per_sweep + 1),

@@ -171,7 +171,12 @@ smcx_status smcx_checkpoint(smcx_lattice* lat, void* buf, size_t* len);
 smcx_status smcx_restore(smcx_lattice* lat, const void* buf, size_t len);
 
 /* Tuning knobs (do not change results, only speed):
-     SMCX_OPT_KERNEL   0 = automatic, 1 = generic (global memory, any lattice),
+     SMCX_OPT_KERNEL   0 = automatic (tuned online: the first colour phases of
+                       smcx_sweep rotate over the kernels and tile shapes
+                       that can run the lattice, each timed with CUDA events
+                       three times, and the fastest is kept; until then the
+                       tiled kernel, else cell, else generic),
+                       1 = generic (global memory, any lattice),
                        2 = tiled (shared-memory tiles + halos, large lattices),
                        3 = cell (one thread per link cell, n_d >= 4)
                        (a sweep fails with EINVAL if the requested kernel
@@ -191,6 +196,14 @@ smcx_status smcx_tile_shape(uint32_t kind, uint32_t i, uint32_t* cells_xyz);
    it, and *tile_shape = the tile shape index (-1 unless tiled).
    ESTATE: no EPI. */
 smcx_status smcx_kernel_in_use(smcx_lattice* lat, uint32_t* kernel, int32_t* tile_shape);
+
+/* State of the online kernel choice: *done = 1 once decided; on entry
+   *n_candidates = capacity of the arrays (may be 0 and the arrays NULL), on
+   return the number of candidates; kernels[c] (1 generic, 2 tiled, 3 cell),
+   shapes[c] (tile shape, -1 unless tiled) and best_ms[c] (fastest timed
+   phase, -1 if not timed yet), each array may be NULL.  ESTATE: no EPI. */
+smcx_status smcx_kernel_tuning(smcx_lattice* lat, uint32_t* done, uint32_t* n_candidates,
+                               uint32_t* kernels, int32_t* shapes, float* best_ms);
 
 /* Releases the handle (never the caller's buffers). */
 smcx_status smcx_destroy(smcx_lattice* lat);

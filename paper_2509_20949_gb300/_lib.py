@@ -133,6 +133,8 @@ SIGNATURES = {
     "smcx_set_option": (_st, [_vp, ctypes.c_uint32, ctypes.c_int64]),
     "smcx_tile_shape_count": (ctypes.c_uint32, [ctypes.c_uint32]),
     "smcx_tile_shape": (_st, [ctypes.c_uint32, ctypes.c_uint32, _P(ctypes.c_uint32)]),
+    "smcx_kernel_tuning": (_st, [_vp, _P(ctypes.c_uint32), _P(ctypes.c_uint32), _P(ctypes.c_uint32),
+                                 _P(ctypes.c_int32), _P(ctypes.c_float)]),
     "smcx_kernel_in_use": (_st, [_vp, _P(ctypes.c_uint32), _P(ctypes.c_int32)]),
     "smcx_destroy": (_st, [_vp]),
     "smcx_last_error": (ctypes.c_char_p, []),

@@ -192,6 +192,22 @@ struct smcx_lattice {
   int n_sm = 0;
   bool tiled_table_ok = false;  // the tiled kernel's int32 difference table fits
   int tiled_kmax = 0;
+  // online kernel choice (SMCX_OPT_KERNEL = 0 and SMCX_OPT_TILE = -1): the
+  // candidates (kernel, tile shape), the fastest phase seen for each, and
+  // the phases timed so far
+  struct Tuning {
+    bool done = false;
+    std::vector<std::pair<int, int>> cands;
+    std::vector<float> best_ms;
+    std::vector<int> samples;
+    uint64_t next = 0;
+    int choice = 0;
+    std::vector<cudaEvent_t> ev;
+  } tune;
+
+  ~smcx_lattice() {
+    for (cudaEvent_t e : tune.ev) cudaEventDestroy(e);
+  }
 
   unsigned long long* stats() { return reinterpret_cast<unsigned long long*>(d_work + wl.stats); }
   int64_t* dV() { return reinterpret_cast<int64_t*>(d_work + wl.V); }
@@ -400,38 +416,68 @@ smcx_status restart_running_energy(smcx_lattice* lat) {
   return full_energy(lat, &lat->E0);
 }
 
-// one colour phase of the current sweep
+// tile shape the tiled kernel uses (-1 if it cannot run the lattice)
 int tiled_shape_for(smcx_lattice* lat) {
   const Geom g = lat->geom();
   if (!lat->tiled_table_ok) return -1;
   if (lat->opt_tile >= 0) return tiled_supported(g, lat->opt_tile) ? lat->opt_tile : -1;
+  if (lat->opt_kernel == 0 && lat->tune.done && lat->tune.cands[lat->tune.choice].first == 2)
+    return lat->tune.cands[lat->tune.choice].second;
   for (int sh = 0; sh < tiled_shape_count(g.kind); ++sh)
     if (tiled_supported(g, sh)) return sh;
   return -1;
 }
 
-// which kernel a colour phase runs: 1 = generic, 2 = tiled, 3 = cell
+bool cell_ok(smcx_lattice* lat) { return lat->tiled_table_ok && cell_supported(lat->geom()); }
+
+// which kernel a colour phase runs: 1 = generic, 2 = tiled, 3 = cell (0 =
+// the requested kernel cannot run the lattice).  Automatic: the tuned
+// choice, and before tuning has finished tiled, else cell, else generic.
 int kernel_choice(smcx_lattice* lat) {
-  const Geom g = lat->geom();
-  const bool cell_ok = lat->tiled_table_ok && cell_supported(g);
   switch (lat->opt_kernel) {
     case 1: return 1;
     case 2: return tiled_shape_for(lat) >= 0 ? 2 : 0;
-    case 3: return cell_ok ? 3 : 0;
+    case 3: return cell_ok(lat) ? 3 : 0;
     default:
+      if (lat->tune.done) return lat->tune.cands[lat->tune.choice].first;
       if (tiled_shape_for(lat) >= 0) return 2;
-      return cell_ok ? 3 : 1;
+      return cell_ok(lat) ? 3 : 1;
   }
 }
 
-// one colour phase of the current sweep
-smcx_status launch_colour(smcx_lattice* lat, int colour, const PhaseArgs& base, const Tables& tab) {
+// candidates of the online choice; with fewer than two it is decided at once
+void tuning_reset(smcx_lattice* lat) {
+  auto& tu = lat->tune;
+  tu.done = false;
+  tu.cands.clear();
+  tu.next = 0;
+  tu.choice = 0;
+  if (lat->has_epi && lat->tiled_table_ok) {
+    const Geom g = lat->geom();
+    for (int sh = 0; sh < tiled_shape_count(g.kind); ++sh)
+      if (tiled_supported(g, sh)) tu.cands.emplace_back(2, sh);
+    if (cell_ok(lat)) tu.cands.emplace_back(3, -1);
+  }
+  if (tu.cands.empty()) tu.cands.emplace_back(1, -1);
+  tu.best_ms.assign(tu.cands.size(), 0.0f);
+  tu.samples.assign(tu.cands.size(), 0);
+  // nothing to decide with one candidate or a kernel / tile shape forced
+  tu.done = tu.cands.size() < 2 || lat->opt_kernel != 0 || lat->opt_tile >= 0;
+}
+
+bool colour_empty(smcx_lattice* lat, int colour) {
+  for (int d = 0; d < 3; ++d)
+    if (lat->m[d] == 1 && ((colour >> d) & 1)) return true;  // no cell of this colour
+  return false;
+}
+
+// one colour phase of the current sweep with kernel `kern` (tiled: shape)
+smcx_status launch_colour_with(smcx_lattice* lat, int colour, const PhaseArgs& base,
+                               const Tables& tab, int kern, int shape) {
   PhaseArgs a = base;
   a.colour = colour;
   const Geom g = lat->geom();
-  for (int d = 0; d < 3; ++d)
-    if (g.m[d] == 1 && ((colour >> d) & 1)) return SMCX_OK;  // no cell of this colour
-  const int kern = kernel_choice(lat);
+  if (colour_empty(lat, colour)) return SMCX_OK;
   if (kern == 0)
     return fail(SMCX_EINVAL, "the requested kernel does not support this lattice/EPI/tile shape");
   if (kern == 3) {
@@ -444,14 +490,19 @@ smcx_status launch_colour(smcx_lattice* lat, int colour, const PhaseArgs& base, 
     TiledEpi te;
     te.kmax = lat->tiled_kmax;
     te.d_table = lat->dtab();
-    SMCX_CUDA(lat, launch_sweep_tiled(g, a, tab, lat->d_occ, te, lat->stats(), tiled_shape_for(lat),
-                                      lat->stream));
+    SMCX_CUDA(lat, launch_sweep_tiled(g, a, tab, lat->d_occ, te, lat->stats(), shape, lat->stream));
     return SMCX_OK;
   }
   const ShellParam sp = shell_param(g.kind);
   SMCX_CUDA(lat, launch_sweep_generic(g, a, sp, tab, lat->d_occ, lat->dV(), lat->stats(),
                                       lat->stream));
   return SMCX_OK;
+}
+
+// one colour phase of the current sweep with the configured kernel
+smcx_status launch_colour(smcx_lattice* lat, int colour, const PhaseArgs& base, const Tables& tab) {
+  const int kern = kernel_choice(lat);
+  return launch_colour_with(lat, colour, base, tab, kern, kern == 2 ? tiled_shape_for(lat) : -1);
 }
 
 // Difference rows of the tiled kernel, one per species pair (p, q) at byte
@@ -617,10 +668,13 @@ smcx_status smcx_set_epi(smcx_lattice* lat, uint32_t n_shells, const int64_t* v_
                                    cudaMemcpyHostToDevice, lat->stream));
   SMCX_CUDA(lat, cudaStreamSynchronize(lat->stream));
   lat->has_epi = true;
+  tuning_reset(lat);
   s = restart_running_energy(lat);
   if (s != SMCX_OK) lat->has_epi = false;
   return s;
 }
+
+constexpr int kTuneSamples = 3;  // timed phases per candidate
 
 smcx_status smcx_sweep(smcx_lattice* lat, uint32_t n_sweeps, double T_first, double T_last,
                        smcx_sweep_stats* out) {
@@ -631,6 +685,17 @@ smcx_status smcx_sweep(smcx_lattice* lat, uint32_t n_sweeps, double T_first, dou
     return fail(SMCX_EINVAL, "temperatures must be >= 0");
   SMCX_CUDA(lat, cudaMemsetAsync(lat->stats() + kStatCall, 0, sizeof(unsigned long long) * 4,
                                  lat->stream));
+  // online kernel choice: while untuned, phases rotate over the candidates
+  // and are timed with events (every candidate gives the same bits)
+  auto& tu = lat->tune;
+  const bool tuning = lat->opt_kernel == 0 && lat->opt_tile < 0 && !tu.done;
+  const size_t max_timed = tuning ? tu.cands.size() * kTuneSamples : 0;
+  std::vector<int> timed;  // candidate of each timed phase
+  while (tu.ev.size() < 2 * max_timed) {
+    cudaEvent_t e;
+    SMCX_CUDA(lat, cudaEventCreate(&e));
+    tu.ev.push_back(e);
+  }
   Tables tab;
   for (uint32_t i = 0; i < n_sweeps; ++i) {
     double T = T_first;
@@ -641,10 +706,39 @@ smcx_status smcx_sweep(smcx_lattice* lat, uint32_t n_sweeps, double T_first, dou
     a.t = lat->t;
     sweep_origin(lat->desc, a.t, a.shift);
     for (int colour = 0; colour < 8; ++colour) {
+      if (tuning && timed.size() < max_timed && !colour_empty(lat, colour)) {
+        const int c = static_cast<int>(tu.next++ % tu.cands.size());
+        const size_t k = timed.size();
+        SMCX_CUDA(lat, cudaEventRecord(tu.ev[2 * k], lat->stream));
+        s = launch_colour_with(lat, colour, a, tab, tu.cands[c].first, tu.cands[c].second);
+        if (s != SMCX_OK) return s;
+        SMCX_CUDA(lat, cudaEventRecord(tu.ev[2 * k + 1], lat->stream));
+        timed.push_back(c);
+        continue;
+      }
       s = launch_colour(lat, colour, a, tab);
       if (s != SMCX_OK) return s;
     }
     lat->t += 1;
+  }
+  if (!timed.empty()) {
+    SMCX_CUDA(lat, cudaEventSynchronize(tu.ev[2 * timed.size() - 1]));
+    for (size_t k = 0; k < timed.size(); ++k) {
+      float ms = 0;
+      SMCX_CUDA(lat, cudaEventElapsedTime(&ms, tu.ev[2 * k], tu.ev[2 * k + 1]));
+      const int c = timed[k];
+      if (tu.samples[c] == 0 || ms < tu.best_ms[c]) tu.best_ms[c] = ms;
+      ++tu.samples[c];
+    }
+    bool all = true;
+    for (int n : tu.samples) all = all && n >= kTuneSamples;
+    if (all) {
+      int best = 0;
+      for (size_t c = 1; c < tu.cands.size(); ++c)
+        if (tu.best_ms[c] < tu.best_ms[best]) best = static_cast<int>(c);
+      tu.choice = best;
+      tu.done = true;
+    }
   }
   if (out) return read_call_stats(lat, out);
   return SMCX_OK;
@@ -854,12 +948,14 @@ smcx_status smcx_set_option(smcx_lattice* lat, uint32_t key, int64_t value) {
   if (key == SMCX_OPT_KERNEL) {
     if (value < 0 || value > 3) return fail(SMCX_EINVAL, "kernel option must be 0..3");
     lat->opt_kernel = static_cast<int>(value);
+    tuning_reset(lat);
     return SMCX_OK;
   }
   if (key == SMCX_OPT_TILE) {
     if (value < -1 || value >= static_cast<int64_t>(smcx_tile_shape_count(lat->desc.kind)))
       return fail(SMCX_EINVAL, "tile shape index out of range");
     lat->opt_tile = static_cast<int>(value);
+    tuning_reset(lat);
     return SMCX_OK;
   }
   return fail(SMCX_EINVAL, "unknown option");
@@ -884,6 +980,22 @@ smcx_status smcx_kernel_in_use(smcx_lattice* lat, uint32_t* kernel, int32_t* til
   if (!lat->has_epi) return fail(SMCX_ESTATE, "no EPI set");
   *kernel = static_cast<uint32_t>(kernel_choice(lat));
   *tile_shape = *kernel == 2 ? tiled_shape_for(lat) : -1;
+  return SMCX_OK;
+}
+
+smcx_status smcx_kernel_tuning(smcx_lattice* lat, uint32_t* done, uint32_t* n_candidates,
+                               uint32_t* kernels, int32_t* shapes, float* best_ms) {
+  if (!lat || !done || !n_candidates) return fail(SMCX_EINVAL, "null argument");
+  if (!lat->has_epi) return fail(SMCX_ESTATE, "no EPI set");
+  const auto& tu = lat->tune;
+  *done = tu.done ? 1u : 0u;
+  const uint32_t cap = *n_candidates;
+  *n_candidates = static_cast<uint32_t>(tu.cands.size());
+  for (uint32_t c = 0; c < cap && c < tu.cands.size(); ++c) {
+    if (kernels) kernels[c] = static_cast<uint32_t>(tu.cands[c].first);
+    if (shapes) shapes[c] = tu.cands[c].second;
+    if (best_ms) best_ms[c] = tu.samples[c] ? tu.best_ms[c] : -1.0f;
+  }
   return SMCX_OK;
 }
 

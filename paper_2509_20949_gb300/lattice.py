@@ -152,6 +152,18 @@ class Lattice:
         check(self.L.smcx_kernel_in_use(self.h, ctypes.byref(k), ctypes.byref(sh)))
         return int(k.value), int(sh.value)
 
+    def kernel_tuning(self):
+        """Online kernel choice: done flag and, per candidate (kernel, tile
+        shape), the fastest timed colour phase in ms (-1 if not timed)."""
+        done, n = ctypes.c_uint32(), ctypes.c_uint32(8)
+        k = (ctypes.c_uint32 * 8)()
+        sh = (ctypes.c_int32 * 8)()
+        ms = (ctypes.c_float * 8)()
+        check(self.L.smcx_kernel_tuning(self.h, ctypes.byref(done), ctypes.byref(n), k, sh, ms))
+        cands = [dict(kernel=int(k[c]), shape=int(sh[c]), best_ms=float(ms[c]))
+                 for c in range(min(int(n.value), 8))]
+        return dict(done=bool(done.value), candidates=cands)
+
     def checkpoint(self) -> bytes:
         n = ctypes.c_size_t()
         check(self.L.smcx_checkpoint(self.h, None, ctypes.byref(n)))

@@ -88,7 +88,7 @@ def test_fcc128_k5_full_size_colour_phases(orc):
     w = inputs.workload("fcc128_k5")
     case = make_case(w["kind"], w["n"], w["K"], w["M"], seed=w["seed"], sigma=w["sigma"],
                      epi_seed=w["epi_seed"], occ_seed=w["occ_seed"], fractions=w["fractions"])
-    lat = gpu_lattice(case)
+    lat = gpu_lattice(case, kernel=TILED)
     assert lat.kernel_in_use()[0] == TILED
     d = oracle_desc(orc, case)
     lat.sweep(1, w["T_first"])  # sweep 0 on the GPU, then replay phases of sweep 1
@@ -113,7 +113,7 @@ def test_bcc812_k5_sampled_cells_and_invariants(orc):
     w = inputs.workload("bcc812_k5")
     case = make_case(w["kind"], w["n"], w["K"], w["M"], seed=w["seed"], sigma=w["sigma"],
                      epi_seed=w["epi_seed"], occ_seed=w["occ_seed"])
-    lat = gpu_lattice(case)
+    lat = gpu_lattice(case, kernel=TILED)
     assert lat.kernel_in_use()[0] == TILED
     d = oracle_desc(orc, case)
     counts0 = np.bincount(case["occ"], minlength=w["K"])
