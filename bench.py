@@ -320,6 +320,7 @@ def run_serve(args):
     m = srv.run_trace(trace, deadline_s=args.window * 3)
     line = {"metric": "attempted MC swaps/sec on 1 GB300 (served, continuous batching)",
             "value": m["swaps_per_s"], "unit": UNIT, "n_gpus": 1, "higher_is_better": True,
+            "finished_jobs_swaps_per_s": m["finished_swaps_per_s"],
             "p50_latency_s": m["p50_latency_s"], "p99_latency_s": m["p99_latency_s"],
             "completed": m["completed"], "submitted": m["submitted"],
             "completed_fraction": m["completed_fraction"], "elapsed_s": m["elapsed_s"],

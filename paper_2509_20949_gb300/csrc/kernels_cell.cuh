@@ -2,9 +2,11 @@
 // active link cell (Sec. 2.2) reading and writing the device storage
 // directly (through L1/L2; lattices of batched jobs are L2-resident).
 //
-// Used where shared-memory tiles do not fit: small and medium lattices, and
-// the batched form, in which one launch runs one colour phase of every job
-// of a batch (blocks map to jobs through a block table).  Works on any
+// Used for small and medium lattices (where it is also faster than the
+// shared-memory tiles: they stay in L2) and for batches of many jobs, whose
+// work items (32 cells of one job and colour phase, one per lane) are run
+// either by one launch per colour phase or by one persistent launch per
+// chunk of sweeps (k_sweep_cells_phase / k_sweep_cells_queue).  Works on any
 // lattice with at least 4 conventional cells per dimension (then no two
 // shell vectors reach the same site, so the swapped pair's mutual bond is
 // the only term to remove from the raw neighbour counts).

@@ -19,6 +19,10 @@ import numpy as np
 from .batch import Batch
 
 
+def _sites(job) -> int:
+    return (2 if job["kind"] == 0 else 4) * int(np.prod(job["n"]))
+
+
 class Server:
     def __init__(self, budget_bytes: int, max_jobs: int = 1024, chunk_sweeps: int = 50,
                  transfer_bytes: int = 1 << 27, clock=time.perf_counter, device=None):
@@ -30,7 +34,9 @@ class Server:
         self.running = {}                  # batch id -> (ticket, job, arrival)
         self.done = {}                     # ticket -> result dict
         self.next_ticket = 0
-        self.swaps = 0                     # attempted swaps of finished jobs
+        self.swaps = 0                     # attempted swaps run on the GPU (all jobs)
+        self.swaps_finished = 0            # of which in jobs that have finished
+        self.progress = {}                 # batch id -> sweeps done
         self.chunks = 0
         self.max_bypass = 64               # how many later jobs may overtake a waiting head
 
@@ -60,6 +66,7 @@ class Server:
                 starving = bypassed >= self.max_bypass
                 continue
             self.running[jid] = (ticket, job, arr)
+            self.progress[jid] = 0
             # every job still waiting ahead of this one has been overtaken once more
             remaining = collections.deque((t, j, a, b + 1) for (t, j, a, b) in remaining)
         self.queue = remaining
@@ -71,6 +78,10 @@ class Server:
             return 0
         self.batch.run(self.chunk)
         self.chunks += 1
+        for jid, (_, job, _) in self.running.items():  # every running job advanced
+            ran = min(self.chunk, job["sweeps"] - self.progress[jid])
+            self.progress[jid] += ran
+            self.swaps += _sites(job) * ran
         finished = self.batch.poll()
         now = self.clock()
         for jid in finished:
@@ -81,8 +92,8 @@ class Server:
             r["arrival_s"] = arr
             r["finish_s"] = now
             self.done[ticket] = r
-            n_sites = (2 if job["kind"] == 0 else 4) * int(np.prod(job["n"]))
-            self.swaps += n_sites * job["sweeps"]
+            self.progress.pop(jid, None)
+            self.swaps_finished += _sites(job) * job["sweeps"]
         return len(finished)
 
     def idle(self) -> bool:
@@ -120,6 +131,7 @@ class Server:
             "p50_latency_s": float(np.percentile(lat, 50)) if len(lat) else None,
             "p99_latency_s": float(np.percentile(lat, 99)) if len(lat) else None,
             "swaps_per_s": self.swaps / elapsed_s if elapsed_s > 0 else 0.0,
+            "finished_swaps_per_s": self.swaps_finished / elapsed_s if elapsed_s > 0 else 0.0,
             "elapsed_s": elapsed_s, "chunks": self.chunks,
         }
 
