@@ -58,6 +58,10 @@ __host__ __device__ constexpr int tiled_row_bytes(int M, int kmax) {
 }  // namespace smcx
 
 namespace smcx {
+// bit-sliced half-shell pair counts of 8-bit lattices (see pair_bits.cu)
+cudaError_t launch_pair_count_bits(const Geom& g, int n_shells, const uint8_t* occ,
+                                   unsigned long long* h, int n_sm, cudaStream_t st,
+                                   bool check_only, bool* ok);
 // tiled half-shell pair counts (see pair_tiled.cu); rows of K_MAX = K <= 5 ? 5 : 6
 cudaError_t launch_pair_count_tiled(const Geom& g, int n_shells, const uint8_t* occ,
                                     unsigned long long* h, int n_sm, cudaStream_t st,

@@ -25,13 +25,17 @@ static cudaError_t pc_k(const Geom& g, const uint8_t* occ, unsigned long long* h
 
 // Half-shell counts H[m][p'][p] (m < n_shells, laid out with K_MAX = 5 or 6
 // species per row) into h (zeroed by the caller); the directed counts are
-// H + H^T.  cudaErrorNotSupported when the lattice needs the generic kernel.
+// H + H^T.  8-bit lattices go to the bit-sliced kernel (pair_bits.cu), 4-bit
+// ones to the byte-tile kernel here.  cudaErrorNotSupported when the lattice
+// needs the generic kernel.
 cudaError_t launch_pair_count_tiled(const Geom& g, int n_shells, const uint8_t* occ,
                                     unsigned long long* h, int n_sm, cudaStream_t st,
                                     bool check_only) {
   bool ok = false;
   cudaError_t e = cudaSuccess;
   if (g.K > 6) return cudaErrorNotSupported;
+  e = launch_pair_count_bits(g, n_shells, occ, h, n_sm, st, check_only, &ok);
+  if (ok || e != cudaSuccess) return e;
   const int M = n_shells < 2 ? 2 : n_shells;
   if (g.kind == 0) {
     if (M == 2) e = pc_k<0, 2>(g, occ, h, n_sm, st, check_only, &ok);
