@@ -1,0 +1,74 @@
+"""Long-run parity (the segment checks of a long anneal): the GPU runs a
+lattice through a 10^4-sweep linear anneal (1200 -> 600 K, the schedule of
+the 1.07e9-site workload) with checkpoints, and from the checkpoints at
+sweeps 0, 5000 and 9997 the oracle replays 3 sweeps that must end in the
+GPU's bits.  On the 1.07e9-site lattice itself, where 3 oracle sweeps take
+far too long, sampled link cells of colour phases after 200 GPU sweeps are
+replayed instead."""
+import numpy as np
+import pytest
+
+from tests.gpu_util import (colour_cells, gpu_lattice, make_case, oracle_desc, require_cuda,
+                            write_region_sites)
+
+pytestmark = pytest.mark.gpu
+
+N_SWEEPS, T0, T1 = 10000, 1200.0, 600.0
+
+
+def anneal_T(t):
+    return T0 + (T1 - T0) * t / (N_SWEEPS - 1)
+
+
+def test_anneal_segments_match_oracle(orc):
+    require_cuda()
+    case = make_case(0, (96, 96, 96), 5, 3, seed=11, sigma=0.02, epi_seed=12, occ_seed=13)
+    lat = gpu_lattice(case)
+    d = oracle_desc(orc, case)
+    # GPU segments [0, 5000), [5000, 9997), [9997, 10000); each call interpolates
+    # its own first and last temperature of the global schedule
+    bounds = [0, 5000, 9997, N_SWEEPS]
+    ckpt = {}
+    for a, b in zip(bounds[:-1], bounds[1:]):
+        ckpt[a] = lat.checkpoint()
+        assert lat.sweep_counter == a
+        lat.sweep(b - a, anneal_T(a), anneal_T(b - 1))
+    final = lat.occupancy()
+    E_final = lat.running_energy()
+    assert E_final == lat.energy()
+    for a in (0, 5000, 9997):
+        lat.restore(ckpt[a])
+        start = lat.occupancy()
+        g = lat.sweep(3, anneal_T(a), anneal_T(a + 2))
+        o_occ, o_st = orc.sweeps(d, case["V"], start, a, 3, anneal_T(a), anneal_T(a + 2))
+        assert np.array_equal(lat.occupancy(), o_occ), a
+        assert g["accepted"] == int(o_st["accepted"].sum()) and g["sum_dE"] == int(o_st["sum_dE"].sum())
+        if a == 9997:
+            assert np.array_equal(o_occ, final)
+            assert lat.running_energy() == E_final
+
+
+def test_bcc812_sampled_cells_after_200_sweeps(orc):
+    """The 1.07e9-site lattice after 200 annealing sweeps on the GPU: 2000
+    sampled link cells of two colour phases of sweep 200 match the oracle."""
+    require_cuda()
+    from paper_2509_20949_gb300 import inputs
+    w = inputs.workload("bcc812_k5")
+    case = make_case(w["kind"], w["n"], w["K"], w["M"], seed=w["seed"], sigma=w["sigma"],
+                     epi_seed=w["epi_seed"], occ_seed=w["occ_seed"])
+    lat = gpu_lattice(case)
+    d = oracle_desc(orc, case)
+    lat.sweep(200, anneal_T(0), anneal_T(199))
+    assert lat.sweep_counter == 200
+    before = lat.occupancy()
+    rng = np.random.default_rng(17)
+    T = anneal_T(200)
+    for colour in (3, 4):
+        lat.run_colour(colour, T)
+        after = lat.occupancy()
+        pick = np.sort(rng.choice(colour_cells(orc, d, colour), 2000, replace=False)).astype(np.uint32)
+        o_occ, _ = orc.phase_cells(d, case["V"], before, 200, T, colour, pick)
+        sites = write_region_sites(orc, d, 200, pick)
+        assert np.array_equal(after[sites], o_occ[sites]), colour
+        before = after
+    assert lat.running_energy() == lat.energy()
