@@ -72,3 +72,60 @@ def test_bcc812_sampled_cells_after_200_sweeps(orc):
         assert np.array_equal(after[sites], o_occ[sites]), colour
         before = after
     assert lat.running_energy() == lat.energy()
+
+
+def test_fcc128_k5_thousand_sweeps_with_sro_checks(orc):
+    """FCC 128^3 x4 = 8.4e6 sites, K = 5 (Dirichlet(5) composition), shells
+    1-4, 800 K, 1000 sweeps: every 100 sweeps the running energy equals the
+    recomputed energy, the species counts are conserved and the SRO
+    parameters satisfy the sum rule; sampled link cells of two colour phases
+    of sweep 1000 match the oracle."""
+    require_cuda()
+    from paper_2509_20949_gb300 import inputs
+    w = inputs.workload("fcc128_k5")
+    case = make_case(w["kind"], w["n"], w["K"], w["M"], seed=w["seed"], sigma=w["sigma"],
+                     epi_seed=w["epi_seed"], occ_seed=w["occ_seed"], fractions=w["fractions"])
+    lat = gpu_lattice(case)
+    d = oracle_desc(orc, case)
+    counts0 = np.bincount(case["occ"], minlength=w["K"])
+    c = counts0 / counts0.sum()
+    for block in range(10):
+        lat.sweep(100, w["T_first"])
+        assert lat.running_energy() == lat.energy()
+        cnt, alpha = lat.sro(w["M"])
+        assert np.array_equal(cnt.sum(axis=(1, 2)),
+                              counts0.sum() * np.array([12, 6, 24, 12], dtype=np.uint64))
+        for m in range(w["M"]):
+            assert np.allclose(alpha[m] @ c, 0.0, atol=1e-12)  # sum_p c_p alpha^{pp'} = 0
+    occ = lat.occupancy()
+    assert np.array_equal(np.bincount(occ, minlength=w["K"]), counts0)
+    rng = np.random.default_rng(29)
+    for colour in (2, 7):
+        lat.run_colour(colour, w["T_first"])
+        after = lat.occupancy()
+        pick = np.sort(rng.choice(colour_cells(orc, d, colour), 3000, replace=False)).astype(np.uint32)
+        o_occ, _ = orc.phase_cells(d, case["V"], occ, 1000, w["T_first"], colour, pick)
+        sites = write_region_sites(orc, d, 1000, pick)
+        assert np.array_equal(after[sites], o_occ[sites]), colour
+        occ = after
+
+
+def test_bcc812_packed_storage_equals_bytes():
+    """The 1.07e9-site lattice in 4-bit packed storage (0.54 GB) runs the same
+    trajectory as in 8-bit storage."""
+    require_cuda()
+    import torch
+    from paper_2509_20949_gb300 import inputs
+    w = inputs.workload("bcc812_k5")
+    case = make_case(w["kind"], w["n"], w["K"], w["M"], seed=w["seed"], sigma=w["sigma"],
+                     epi_seed=w["epi_seed"], occ_seed=w["occ_seed"])
+    res = []
+    for pack in (8, 4):
+        lat = gpu_lattice(case, pack_bits=pack)
+        st = lat.sweep(2, anneal_T(0), anneal_T(1))
+        res.append((lat.occupancy(), st, lat.running_energy()))
+        lat.close()
+        del lat
+        torch.cuda.empty_cache()
+    assert res[0][1] == res[1][1] and res[0][2] == res[1][2]
+    assert np.array_equal(res[0][0], res[1][0])
