@@ -418,7 +418,7 @@ def main():
         lat.set_occupancy(h_in.numpy())
         step(args.warmup + args.steps + s)
         cnt, _ = lat.sro(M)
-        h_out.numpy()[:] = lat.occupancy()
+        lat.occupancy(out=h_out.numpy())  # device-to-host straight into pinned memory
         h_in, h_out = h_out, h_in
     torch.cuda.synchronize()
     e2e_s = time.perf_counter() - t0

@@ -119,8 +119,14 @@ class Lattice:
         check(self.L.smcx_warren_cowley_sro(self.h, int(n_shells), _host_ptr(cnt), _host_ptr(alpha)))
         return cnt, alpha
 
-    def occupancy(self) -> np.ndarray:
-        out = np.empty(self.N, dtype=np.uint8)
+    def occupancy(self, out: np.ndarray | None = None) -> np.ndarray:
+        """Canonical occupancy (N bytes).  `out`: a contiguous uint8 array
+        of N bytes to fill (e.g. a view of pinned host memory, which the
+        device-to-host copy then reaches directly)."""
+        if out is None:
+            out = np.empty(self.N, dtype=np.uint8)
+        elif out.dtype != np.uint8 or out.size != self.N or not out.flags["C_CONTIGUOUS"]:
+            raise ValueError("out must be a contiguous uint8 array of N bytes")
         check(self.L.smcx_get_occupancy(self.h, _host_ptr(out)))
         return out
 

@@ -127,3 +127,18 @@ def test_checkpoint_resume_is_byte_exact(orc):
     bad[100] ^= 1
     with pytest.raises(Exception):
         b.restore(bytes(bad))
+
+
+def test_occupancy_into_caller_buffer():
+    """get_occupancy fills a caller's (pinned) host buffer directly."""
+    require_cuda()
+    import torch
+    case = make_case(0, (12, 10, 8), 4, 2, seed=5)
+    lat = gpu_lattice(case)
+    lat.sweep(2, 900.0)
+    ref = lat.occupancy()
+    pinned = torch.empty(lat.N, dtype=torch.uint8, pin_memory=True)
+    got = lat.occupancy(out=pinned.numpy())
+    assert got.ctypes.data == pinned.data_ptr() and np.array_equal(pinned.numpy(), ref)
+    with pytest.raises(ValueError):
+        lat.occupancy(out=np.empty(lat.N - 1, dtype=np.uint8))
