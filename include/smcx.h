@@ -282,6 +282,27 @@ smcx_status smcx_batch_set_option(smcx_batch* b, uint32_t key, int64_t value);
 smcx_status smcx_batch_tuning(smcx_batch* b, int32_t* tile, int32_t* schedule, int32_t* occupancy,
                               uint32_t* tuned);
 
+/* Replica exchange (parallel tempering, Sec. 2.2, Eqs. 6-7) between jobs
+   that simulate the same system (same descriptor, shells and EPI) at
+   different temperatures.  ladder[0..n) (in/out) = job ids, ladder[k] being
+   the job at the k-th temperature of the ladder.  Round `round` attempts the
+   neighbour pairs (k, k+1) for k = round mod 2, round mod 2 + 2, ...:
+   Delta = (beta_k - beta_{k+1}) (E_k - E_{k+1}), beta = 1/(k_B T) (k_B =
+   8.617333262e-5 eV/K), E the jobs' exact running energies (q units; the
+   difference is formed in integers and scaled by 2^-32 to eV); accepted iff
+   Delta >= 0 or u < exp(Delta), u in [0, 1) from the 53 high bits of words
+   0 and 1 of Philox4x32-10(counter = (k, round, 0, 3), key = seed).  An
+   accepted pair exchanges the two jobs' temperatures and their ladder
+   entries (so ladder[k] is again the job at the k-th temperature).
+   *n_accepted (may be NULL) = accepted pairs.  Call between runs; it
+   synchronises.  EINVAL: fewer than 2 jobs, unknown or repeated ids, jobs
+   of different systems, a temperature that is 0 or infinite. */
+smcx_status smcx_batch_exchange(smcx_batch* b, uint32_t* ladder, uint32_t n, uint64_t seed,
+                                uint32_t round, uint32_t* n_accepted);
+
+/* Current temperature of a job (changes through smcx_batch_exchange). */
+smcx_status smcx_batch_temperature(smcx_batch* b, uint32_t job_id, double* T);
+
 /* Work-queue statistics since the batch was created: out[0] = work items
    that had to wait for the previous colour phase of their job, out[1] =
    polls of those waits, out[2] = nanoseconds they waited (summed over

@@ -116,6 +116,10 @@ def _load():
                                             ctypes.c_uint32, ctypes.c_double, ctypes.c_int,
                                             P(ctypes.c_uint32), ctypes.c_uint32, P(_Stats)]
             lib.orc_sweep_shift.argtypes = [P(_Desc), ctypes.c_uint32, P(ctypes.c_int32)]
+            lib.orc_exchange.argtypes = [ctypes.c_uint32, P(ctypes.c_int64), P(ctypes.c_double),
+                                         ctypes.c_uint64, ctypes.c_uint32, P(ctypes.c_uint32),
+                                         P(ctypes.c_uint8)]
+            lib.orc_exchange.restype = ctypes.c_int
             for name in ("orc_shells", "orc_layout", "orc_thresholds", "orc_energy",
                          "orc_pair_counts", "orc_sro_alpha", "orc_delta_e", "orc_sweeps",
                          "orc_phase_cells"):
@@ -296,3 +300,19 @@ def sweep_shift(desc: Desc, t: int):
 
 def species_counts(occ, K: int) -> np.ndarray:
     return np.bincount(np.asarray(occ, dtype=np.uint8).ravel(), minlength=K).astype(np.uint64)
+
+
+def exchange(E, T, seed: int, rnd: int, perm):
+    """Replica exchange round (Sec. 2.2, Eqs. 6-7): E[r] = energy of replica
+    r (q units), T[k] = k-th temperature, perm[k] = replica at T[k].
+    Returns (new perm, accepted flags per pair (k, k+1))."""
+    lib = _load()
+    n = len(T)
+    e = np.ascontiguousarray(E, dtype=np.int64)
+    t = np.ascontiguousarray(T, dtype=np.float64)
+    p = np.ascontiguousarray(perm, dtype=np.uint32).copy()
+    acc = np.zeros(n, dtype=np.uint8)
+    _check(lib.orc_exchange(n, _ptr(e, ctypes.c_int64), _ptr(t, ctypes.c_double), int(seed),
+                            int(rnd), _ptr(p, ctypes.c_uint32), _ptr(acc, ctypes.c_uint8)),
+           "exchange")
+    return p, acc[: n - 1].astype(bool)

@@ -667,3 +667,43 @@ void orc_sweep_shift(const orc_desc *d, uint32_t t, int32_t *s) {
   s[1] = v[1];
   s[2] = v[2];
 }
+
+/* ------------------------------------------------------------------------ */
+/* Replica exchange (parallel tempering, Sec. 2.2, Eqs. 6-7).  Replicas of   */
+/* one system run at temperatures T[0..n); perm[k] is the replica currently  */
+/* at temperature T[k], E[r] its energy (q units).  Round `round` attempts   */
+/* the neighbour pairs (k, k+1) with k = round mod 2, round mod 2 + 2, ...:  */
+/*   Delta = (1/k_B)(1/T_k - 1/T_{k+1}) (E_{perm[k]} - E_{perm[k+1]}) [eV],   */
+/*   accepted with probability min(1, exp(Delta)) (Eq. 6), i.e. iff         */
+/*   Delta >= 0 or u < exp(Delta), u uniform in [0, 1) from the 53 high bits */
+/*   of words 0, 1 of Philox(counter = (k, round, 0, 3), key = seed);        */
+/* an accepted pair exchanges its replicas' temperatures (perm[k] and        */
+/* perm[k+1] swap).  acc[k] = 1 for an accepted pair (k, k+1), else 0.       */
+/* Reading: beta = 1/(k_B T) as for the acceptance tables, the energy        */
+/* difference formed exactly in integers and scaled by 2^-32 to eV.          */
+/* ------------------------------------------------------------------------ */
+int orc_exchange(uint32_t n, const int64_t *E, const double *T, uint64_t seed, uint32_t round,
+                 uint32_t *perm, uint8_t *acc) {
+  if (n < 2) return ORC_EINVAL;
+  for (uint32_t k = 0; k < n; ++k) {
+    if (!(T[k] > 0) || isinf(T[k]) || perm[k] >= n) return ORC_EINVAL;
+    acc[k] = 0;
+  }
+  for (uint32_t k = round % 2; k + 1 < n; k += 2) {
+    const double beta_a = 1.0 / (ORC_KB * T[k]);
+    const double beta_b = 1.0 / (ORC_KB * T[k + 1]);
+    const __int128 diff = (__int128)E[perm[k]] - (__int128)E[perm[k + 1]];
+    const double de_ev = ldexp((double)diff, -32);
+    const double delta = (beta_a - beta_b) * de_ev;
+    uint32_t w[4];
+    philox_keyed(k, round, 0u, 3u, seed, w);
+    const double u = ldexp((double)((((uint64_t)w[0] << 32) | w[1]) >> 11), -53);
+    if (delta >= 0.0 || u < exp(delta)) {
+      const uint32_t t = perm[k];
+      perm[k] = perm[k + 1];
+      perm[k + 1] = t;
+      acc[k] = 1;
+    }
+  }
+  return ORC_OK;
+}

@@ -158,6 +158,9 @@ SIGNATURES = {
                                 _P(ctypes.c_uint32)]),
     "smcx_batch_tile_shape": (_st, [ctypes.c_uint32, _P(ctypes.c_uint32)]),
     "smcx_batch_queue_stats": (_st, [_vp, _P(ctypes.c_uint64)]),
+    "smcx_batch_exchange": (_st, [_vp, _P(ctypes.c_uint32), ctypes.c_uint32, ctypes.c_uint64,
+                                  ctypes.c_uint32, _P(ctypes.c_uint32)]),
+    "smcx_batch_temperature": (_st, [_vp, ctypes.c_uint32, _P(ctypes.c_double)]),
     "smcx_pair_counts_noalloc": (_st, [ctypes.c_uint32, _P(ctypes.c_uint32), ctypes.c_uint32,
                                        ctypes.c_uint32, _vp, _vp, _vp]),
     "smcx_philox4x32_10": (None, [_P(ctypes.c_uint32), _P(ctypes.c_uint32), _P(ctypes.c_uint32)]),

@@ -142,3 +142,19 @@ class Batch:
         out = (ctypes.c_uint64 * 3)()
         check(self.L.smcx_batch_queue_stats(self.h, out))
         return dict(waited_items=int(out[0]), polls=int(out[1]), wait_ns=int(out[2]))
+
+    # replica exchange ------------------------------------------------------
+    def exchange(self, ladder, seed: int, rnd: int):
+        """One replica-exchange round (Sec. 2.2, Eqs. 6-7) over `ladder`
+        (job ids, ladder[k] = the job at the k-th temperature).  Returns the
+        new ladder and the number of accepted pairs."""
+        lad = (ctypes.c_uint32 * len(ladder))(*[int(j) for j in ladder])
+        acc = ctypes.c_uint32()
+        check(self.L.smcx_batch_exchange(self.h, lad, len(ladder), int(seed), int(rnd),
+                                         ctypes.byref(acc)))
+        return [int(v) for v in lad], int(acc.value)
+
+    def temperature(self, job_id: int) -> float:
+        t = ctypes.c_double()
+        check(self.L.smcx_batch_temperature(self.h, int(job_id), ctypes.byref(t)))
+        return float(t.value)

@@ -718,6 +718,80 @@ smcx_status smcx_batch_tuning(smcx_batch* b, int32_t* tile, int32_t* schedule, i
   return SMCX_OK;
 }
 
+// Replica exchange (parallel tempering, Sec. 2.2, Eqs. 6-7) between jobs
+// that simulate one system at different temperatures: ladder[k] is the job at
+// the k-th temperature.  Round r attempts the neighbour pairs (k, k+1),
+// k = r mod 2, r mod 2 + 2, ...; Delta = (beta_k - beta_{k+1}) (E_k -
+// E_{k+1}) with beta = 1/(k_B T) and the jobs' exact running energies
+// (difference in integers, scaled by 2^-32 to eV); a pair is accepted iff
+// Delta >= 0 or u < exp(Delta), u from the 53 high bits of words 0, 1 of
+// Philox(counter = (k, r, 0, 3), key = seed).  An accepted pair exchanges the
+// two jobs' temperatures (tables included) and its ladder entries.
+smcx_status smcx_batch_exchange(smcx_batch* b, uint32_t* ladder, uint32_t n, uint64_t seed,
+                                uint32_t round, uint32_t* n_accepted) {
+  smcx_status s = bcheck(b);
+  if (s != SMCX_OK) return s;
+  if (!ladder || n < 2) return batch_fail(SMCX_EINVAL, "exchange needs a ladder of >= 2 jobs");
+  std::vector<bool> seen(b->max_jobs, false);
+  for (uint32_t k = 0; k < n; ++k) {
+    const uint32_t id = ladder[k];
+    if (id >= b->max_jobs || !b->jobs[id].used || seen[id])
+      return batch_fail(SMCX_EINVAL, "exchange: unknown or repeated job id");
+    seen[id] = true;
+    const Job& j = b->jobs[id];
+    const Job& j0 = b->jobs[ladder[0]];
+    if (!(j.T > 0) || std::isinf(j.T))
+      return batch_fail(SMCX_EINVAL, "exchange: temperatures must be finite and > 0");
+    if (j.desc.kind != j0.desc.kind || j.desc.n_species != j0.desc.n_species || j.M != j0.M ||
+        j.desc.n[0] != j0.desc.n[0] || j.desc.n[1] != j0.desc.n[1] || j.desc.n[2] != j0.desc.n[2] ||
+        j.V != j0.V)
+      return batch_fail(SMCX_EINVAL, "exchange: the jobs do not simulate the same system");
+  }
+  std::vector<unsigned long long> st(8ull * b->max_jobs);
+  BATCH_CUDA(b, cudaMemcpyAsync(st.data(), b->stats(0), sizeof(unsigned long long) * st.size(),
+                                cudaMemcpyDeviceToHost, b->stream));
+  BATCH_CUDA(b, cudaStreamSynchronize(b->stream));
+  auto energy = [&](uint32_t id) {
+    return b->jobs[id].E0 + static_cast<int64_t>(st[8ull * id + kStatCum + 3]);
+  };
+  constexpr double kB = 8.617333262e-5;  // eV/K, as for the acceptance tables
+  uint32_t acc = 0;
+  for (uint32_t k = round % 2; k + 1 < n; k += 2) {
+    Job& a = b->jobs[ladder[k]];
+    Job& c = b->jobs[ladder[k + 1]];
+    const double beta_a = 1.0 / (kB * a.T), beta_c = 1.0 / (kB * c.T);
+    const __int128 diff = static_cast<__int128>(energy(ladder[k])) - energy(ladder[k + 1]);
+    const double delta = (beta_a - beta_c) * std::ldexp(static_cast<double>(diff), -32);
+    const U4 w = philox4x32_10(k, round, 0u, 3u, static_cast<uint32_t>(seed),
+                               static_cast<uint32_t>(seed >> 32));
+    const double u =
+        std::ldexp(static_cast<double>(((static_cast<uint64_t>(w.x) << 32) | w.y) >> 11), -53);
+    if (!(delta >= 0.0 || u < std::exp(delta))) continue;
+    std::swap(a.T, c.T);
+    for (uint32_t id : {ladder[k], ladder[k + 1]}) {
+      Job& j = b->jobs[id];
+      Tables tab;
+      host_build_tables(j.T, &tab, &j.mode, &j.sbin);
+      BATCH_CUDA(b, cudaMemcpyAsync(b->at(b->cl.tabs) + kTabBytes * id, tab.w, kTabBytes,
+                                    cudaMemcpyHostToDevice, b->stream));
+    }
+    std::swap(ladder[k], ladder[k + 1]);
+    ++acc;
+  }
+  BATCH_CUDA(b, cudaStreamSynchronize(b->stream));  // the tables' host copies go out of scope
+  if (n_accepted) *n_accepted = acc;
+  return SMCX_OK;
+}
+
+smcx_status smcx_batch_temperature(smcx_batch* b, uint32_t job_id, double* T) {
+  smcx_status s = bcheck(b);
+  if (s != SMCX_OK) return s;
+  if (job_id >= b->max_jobs || !b->jobs[job_id].used || !T)
+    return batch_fail(SMCX_EINVAL, "unknown job or null output");
+  *T = b->jobs[job_id].T;
+  return SMCX_OK;
+}
+
 smcx_status smcx_batch_queue_stats(smcx_batch* b, uint64_t* out) {
   smcx_status s = bcheck(b);
   if (s != SMCX_OK) return s;
