@@ -429,7 +429,13 @@ def main():
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(w, N, V, occ, args.cpu_seconds, rank)
-    traffic = _recorded_traffic() if args.workload == "bcc812_k5" and args.pack_bits == 8 else None
+    rec = _recorded_profile() if args.workload == "bcc812_k5" and args.pack_bits == 8 else None
+    traffic = rec["dram_bytes_per_launch"] if rec else None
+    # unlike and accepted fractions of the trials of one more sweep (outside the timed region)
+    ts = lat.sweep(1, sweep_temperature(w, args.warmup + args.steps + args.e2e_steps))
+    trial_stats = {"unlike_frac": ts["unlike"] / ts["attempts"],
+                   "accepted_frac": ts["accepted"] / ts["attempts"],
+                   "accepted_per_unlike": ts["accepted"] / max(1, ts["unlike"])}
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -443,8 +449,10 @@ def main():
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic,
                          "kernel": "sweep phase", "kernel_ms_per_launch": kernel_ms,
-                         "peak_source": peak_src},
+                         "peak_source": peak_src,
+                         "limiter": rec.get("limiter") if rec else None},
             "kernel_choice": kernel_choice,
+            "trial_stats": trial_stats,
             "cpu_baseline": cpu,
             "clocks": clk,
             # per step: 8 colour phases + the pair count (8-bit storage, K <= 6:
@@ -458,9 +466,10 @@ def main():
     return 0
 
 
-def _recorded_traffic():
-    """DRAM bytes per phase launch of the tiled sweep from the committed ncu
-    summary, if it was taken on the current kernel source (else None)."""
+def _recorded_profile():
+    """Figures of the committed ncu summary of the tiled sweep phase (DRAM
+    bytes per launch, shared-memory pipe and issue utilisation), if it was
+    taken on the current kernel source (else None)."""
     import hashlib
     import re
 
@@ -475,7 +484,19 @@ def _recorded_traffic():
     m_b = re.search(r"dram_bytes_per_launch: ([0-9]+)", text)
     if not m_sha or not m_b or m_sha.group(1) != sha:
         return None
-    return int(m_b.group(1))
+    out = {"dram_bytes_per_launch": int(m_b.group(1))}
+    m_s = re.search(r"shared wavefronts \| [0-9.]+M \(([0-9.]+)% of the shared pipe", text)
+    m_i = re.search(r"\| issue active \| ([0-9.]+)%", text)
+    if m_s and m_i:
+        out["limiter"] = {"unit": "shared-memory pipe", "frac": float(m_s.group(1)) / 100.0,
+                          "issue_active_frac": float(m_i.group(1)) / 100.0,
+                          "source": "profiles/sweep_tiled_bcc812_k5.md"}
+    return out
+
+
+def _recorded_traffic():
+    rec = _recorded_profile()
+    return rec["dram_bytes_per_launch"] if rec else None
 
 
 if __name__ == "__main__":
