@@ -275,6 +275,12 @@ smcx_status smcx_batch_run(smcx_batch* b, uint32_t chunk_sweeps, uint32_t* n_fin
 #define SMCX_BATCH_OPT_TILE 1u
 #define SMCX_BATCH_OPT_OCCUPANCY 2u
 #define SMCX_BATCH_OPT_SCHEDULE 3u
+/* Testing aid for failure detection (value 1 arms it): the next run with the
+   persistent-queue schedule tells the kernel that the first active job has
+   one work item per phase more than it has, so the waits for that job's
+   earlier phases give up after their limit (about 2 s); the run returns
+   ETIMEOUT and the batch stays in an error state.  Nothing faults or hangs. */
+#define SMCX_BATCH_OPT_TEST_WAIT_TIMEOUT 4u
 smcx_status smcx_batch_set_option(smcx_batch* b, uint32_t key, int64_t value);
 
 /* Current choice: *tile, *schedule and *occupancy (-1 while tuning), *tuned

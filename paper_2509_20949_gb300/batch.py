@@ -115,7 +115,7 @@ class Batch:
                     largest_free=int(lb.value))
 
     # tuning (never changes results) ---------------------------------------
-    OPT_TILE, OPT_OCCUPANCY, OPT_SCHEDULE = 1, 2, 3
+    OPT_TILE, OPT_OCCUPANCY, OPT_SCHEDULE, OPT_TEST_WAIT_TIMEOUT = 1, 2, 3, 4
 
     def set_option(self, key: int, value: int):
         """key OPT_TILE (work-item shape index), OPT_SCHEDULE (0 persistent

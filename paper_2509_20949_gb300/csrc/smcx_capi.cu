@@ -10,6 +10,7 @@
 
 #include "../../include/smcx.h"
 #include "kernels.h"
+#include "trace.h"
 
 using namespace smcx;
 
@@ -351,6 +352,7 @@ smcx_status download_occupancy(smcx_lattice* lat, uint8_t* h) {
 }
 
 smcx_status run_pair_counts(smcx_lattice* lat, uint32_t n_shells, std::vector<uint64_t>* out) {
+  TraceRange trace("smcx_pair_counts");
   const size_t K = lat->desc.n_species;
   const size_t n_cnt = n_shells * K * K;
   Geom g = lat->geom();
@@ -474,6 +476,7 @@ bool colour_empty(smcx_lattice* lat, int colour) {
 // one colour phase of the current sweep with kernel `kern` (tiled: shape)
 smcx_status launch_colour_with(smcx_lattice* lat, int colour, const PhaseArgs& base,
                                const Tables& tab, int kern, int shape) {
+  TraceRange trace("smcx_colour_phase");
   PhaseArgs a = base;
   a.colour = colour;
   const Geom g = lat->geom();
@@ -678,6 +681,7 @@ constexpr int kTuneSamples = 3;  // timed phases per candidate
 
 smcx_status smcx_sweep(smcx_lattice* lat, uint32_t n_sweeps, double T_first, double T_last,
                        smcx_sweep_stats* out) {
+  TraceRange trace("smcx_sweep");
   smcx_status s = check_handle(lat);
   if (s != SMCX_OK) return s;
   if (!lat->has_epi) return fail(SMCX_ESTATE, "set_epi must be called before sweep");
