@@ -217,11 +217,13 @@ def run_reference(args):
     oracle.build()
     d = oracle.Desc(w["kind"], w["n"], w["K"], w["M"], seed=w["seed"])
     cids = _colour_cells(oracle, d, 0)
-    per_step = max(64, min(32768, len(cids) // max(1, args.steps + args.warmup)))
+    per_step = min(len(cids), max(64, min(32768, len(cids) // max(1, args.steps + args.warmup))))
     scratch = np.array(occ, copy=True)
     pos = 0
     times, atts = [], []
     for s in range(args.warmup + args.steps):
+        if pos + per_step > len(cids):  # small lattices: go round the colour's cells again
+            pos = 0
         sel = cids[pos:pos + per_step]
         pos += per_step
         t0 = time.perf_counter()

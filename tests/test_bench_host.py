@@ -1,0 +1,29 @@
+"""bench.py pieces that run on the host: the reference arm (the oracle timed
+on a bounded sample of the workload) reports a positive rate on a lattice
+smaller than its per-step sample, and the recorded-profile reader."""
+import json
+import subprocess
+import sys
+import os
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def test_reference_arm_on_a_small_lattice():
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference",
+                        "--workload", "bcc16_k4", "--steps", "3", "--warmup", "3"],
+                       capture_output=True, text=True, timeout=300, cwd=ROOT)
+    assert r.returncode == 0, r.stderr
+    line = json.loads(r.stdout.strip().splitlines()[-1])
+    assert line["impl"] == "reference" and line["value"] > 0
+    assert line["cpu_baseline"]["value"] == line["value"] and line["cpu_baseline"]["cores"] == 1
+    assert line["e2e"]["h2d_bytes_per_step"] == 0
+
+
+def test_recorded_profile_matches_kernel_source():
+    sys.path.insert(0, ROOT)
+    import bench
+    rec = bench._recorded_profile()
+    # the committed ncu summary was taken on the current tiled-kernel source
+    assert rec is not None and rec["dram_bytes_per_launch"] > 0
+    assert 0 < rec["limiter"]["frac"] <= 1 and 0 < rec["limiter"]["issue_active_frac"] <= 1
