@@ -46,6 +46,9 @@ struct CCfg {
   static constexpr int RSTEP = ROWB / W;
   static constexpr int DBYTES = KMAX * KMAX * ROWB;
   static constexpr int NT = 128;
+  // resident blocks per SM the register budget allows: FCC with 3-4 shells
+  // and BCC with 4 shells spill at 128 registers, so they get 170
+  static constexpr int MINB = ((KIND == 1 && M >= 3) || (KIND == 0 && M >= 4)) ? 3 : 4;
   static constexpr int D_OFF = 4 * kTabWords;                         // shared layout
   static constexpr int PT_OFF = round_up(D_OFF + DBYTES, 16);
   static constexpr int SMEM = PT_OFF + 4 * NB * Z1;
@@ -332,7 +335,7 @@ __device__ __forceinline__ void load_tables(uint8_t* smem, const uint32_t* tab, 
 
 // one colour phase of one lattice (plain path)
 template <class C>
-__global__ void __launch_bounds__(C::NT, 4) k_sweep_cells_single(const __grid_constant__ Geom g,
+__global__ void __launch_bounds__(C::NT, C::MINB) k_sweep_cells_single(const __grid_constant__ Geom g,
                                                               const PhaseArgs a,
                                                               const __grid_constant__ Tables tab,
                                                               uint8_t* __restrict__ occ,
