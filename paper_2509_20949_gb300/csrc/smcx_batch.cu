@@ -316,7 +316,8 @@ uint32_t longest_cell(const Job& j) {
 
 // queue order and the first item of each job within a phase, for tile
 // `tile`: jobs with the longest chains of dependent trials first (their
-// phases bound the chunk), then the larger ones, then by slot
+// phases bound the chunk), jobs of one kernel variant together (neighbouring
+// blocks then run the same code), then the larger ones, then by slot
 smcx_status build_queue(smcx_batch* b, int tile) {
   b->order.clear();
   for (uint32_t slot = 0; slot < b->max_jobs; ++slot) {
@@ -328,6 +329,8 @@ smcx_status build_queue(smcx_batch* b, int tile) {
     const Job& c = b->jobs[y];
     const uint32_t la = longest_cell(a), lc = longest_cell(c);
     if (la != lc) return la > lc;
+    const int va = cell_variant(a.g), vc = cell_variant(c.g);  // neighbouring blocks, same code
+    if (va != vc) return va < vc;
     return job_items(a, tile, nullptr, nullptr) > job_items(c, tile, nullptr, nullptr);
   });
   std::vector<uint32_t> first;
