@@ -131,6 +131,11 @@ def workload(name: str) -> dict:
     if name == "bcc812_k5":     # BCC 812^3 x2 = 1.07e9 sites, 5 species, shells 1-3, anneal
         return dict(kind=BCC, n=(812, 812, 812), K=5, M=3, sigma=0.02, epi_seed=0, seed=0,
                     fractions=None, occ_seed=0, T_first=1200.0, T_last=600.0, sweeps=10000)
+    if name == "fcc672_k5":     # the paper's production lattice: FCC 672x630x630 x4 = 1.07e9 sites,
+        # Fe29Co29Ni28Al7Ti7 composition, 2000 -> 1000 K anneal (Sec. 3.2); synthetic EPIs, shells 1-4
+        return dict(kind=FCC, n=(672, 630, 630), K=5, M=4, sigma=0.03, epi_seed=0, seed=0,
+                    fractions=[0.29, 0.29, 0.28, 0.07, 0.07], occ_seed=0, T_first=2000.0,
+                    T_last=1000.0, sweeps=3000000)
     if name == "bcc448_k5":     # the same recipe on 448^3 x2 = 1.8e8 sites (> L2): profiling case
         return dict(kind=BCC, n=(448, 448, 448), K=5, M=3, sigma=0.02, epi_seed=0, seed=0,
                     fractions=None, occ_seed=0, T_first=1200.0, T_last=600.0, sweeps=10000)
