@@ -151,6 +151,32 @@ smcx_status smcx_get_occupancy(smcx_lattice* lat, uint8_t* h_out);
    sweep counter is unchanged.  Synchronises. */
 smcx_status smcx_set_occupancy(smcx_lattice* lat, const uint8_t* h_in);
 
+/* Composition profile along a cylinder (the atom-probe-like analysis of
+   Sec. 3.2, whose cylinders are r = 12a, l = 72a): positions in half units
+   h = a/2 (site 2*(x,y,z) + basis).  The cylinder's axis is lattice axis
+   `axis` (0 = x, 1 = y, 2 = z) through origin_h[3]; a site at h is inside
+   when t = (h_axis - origin_axis) mod 2n_axis < length_h and the squared
+   minimum-image distance to the axis (each other component taken in
+   (-n_d, n_d] modulo 2n_d) is <= radius2_h.  counts[bin][K] (host, n_bins
+   x K) receives the species counts per bin, bin = t * n_bins / length_h.
+   EINVAL: axis > 2, length_h outside 1..2n_axis, n_bins = 0, n_bins * K >
+   8192 or 8 n_bins K > sites.  Synchronises. */
+smcx_status smcx_composition_profile(smcx_lattice* lat, uint32_t axis, const int32_t* origin_h,
+                                     uint64_t radius2_h, uint32_t length_h, uint32_t n_bins,
+                                     uint64_t* counts);
+
+/* Clusters (precipitates, Sec. 3.2): connected components of the sites whose
+   species s has bit s set in species_mask, two such sites being connected
+   when they are first-shell neighbours (periodic).  d_scratch: caller's
+   device buffer of >= 8 bytes per site, 16-byte aligned (contents
+   overwritten).  *n_clusters = number of clusters; sizes[0..min(cap,
+   n_clusters)) (host) = the largest cluster sizes in descending order.
+   ETIMEOUT: a capped device loop gave up (the handle then stays in error).
+   Synchronises. */
+smcx_status smcx_clusters(smcx_lattice* lat, uint32_t species_mask, void* d_scratch,
+                          size_t scratch_bytes, uint64_t* n_clusters, uint64_t* sizes,
+                          uint64_t cap);
+
 /* Sweep counter (the global sweep index t of the next sweep). */
 smcx_status smcx_get_sweep_counter(smcx_lattice* lat, uint32_t* t);
 smcx_status smcx_set_sweep_counter(smcx_lattice* lat, uint32_t t);

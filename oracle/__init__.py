@@ -120,6 +120,13 @@ def _load():
                                          ctypes.c_uint64, ctypes.c_uint32, P(ctypes.c_uint32),
                                          P(ctypes.c_uint8)]
             lib.orc_exchange.restype = ctypes.c_int
+            lib.orc_profile.argtypes = [P(_Desc), P(ctypes.c_uint8), ctypes.c_int, P(ctypes.c_int32),
+                                        ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32,
+                                        P(ctypes.c_uint64)]
+            lib.orc_profile.restype = ctypes.c_int
+            lib.orc_clusters.argtypes = [P(_Desc), P(ctypes.c_uint8), ctypes.c_uint32,
+                                         P(ctypes.c_uint64), P(ctypes.c_uint64)]
+            lib.orc_clusters.restype = ctypes.c_int
             for name in ("orc_shells", "orc_layout", "orc_thresholds", "orc_energy",
                          "orc_pair_counts", "orc_sro_alpha", "orc_delta_e", "orc_sweeps",
                          "orc_phase_cells"):
@@ -316,3 +323,32 @@ def exchange(E, T, seed: int, rnd: int, perm):
                             int(rnd), _ptr(p, ctypes.c_uint32), _ptr(acc, ctypes.c_uint8)),
            "exchange")
     return p, acc[: n - 1].astype(bool)
+
+
+def composition_profile(desc: Desc, occ, axis: int, origin_h, radius2_h: int, length_h: int,
+                        n_bins: int) -> np.ndarray:
+    """Species counts [n_bins][K] along a cylinder (atom-probe-like
+    analysis, Sec. 3.2); positions in half lattice-constant units."""
+    lib = _load()
+    o = _occ(occ)
+    org = np.ascontiguousarray(origin_h, dtype=np.int32)
+    out = np.zeros((n_bins, desc.K), dtype=np.uint64)
+    _check(lib.orc_profile(ctypes.byref(desc.c()), _ptr(o, ctypes.c_uint8), int(axis),
+                           _ptr(org, ctypes.c_int32), int(radius2_h), int(length_h), int(n_bins),
+                           _ptr(out, ctypes.c_uint64)), "profile")
+    return out
+
+
+def clusters(desc: Desc, occ, species) -> np.ndarray:
+    """Sizes (descending) of the first-shell-connected clusters of the sites
+    whose species is in `species` (precipitates, Sec. 3.2)."""
+    lib = _load()
+    o = _occ(occ)
+    mask = 0
+    for sp in species:
+        mask |= 1 << int(sp)
+    sizes = np.zeros(max(1, o.size), dtype=np.uint64)
+    n = ctypes.c_uint64()
+    _check(lib.orc_clusters(ctypes.byref(desc.c()), _ptr(o, ctypes.c_uint8), mask,
+                            _ptr(sizes, ctypes.c_uint64), ctypes.byref(n)), "clusters")
+    return sizes[: int(n.value)]

@@ -707,3 +707,105 @@ int orc_exchange(uint32_t n, const int64_t *E, const double *T, uint64_t seed, u
   }
   return ORC_OK;
 }
+
+/* ------------------------------------------------------------------------ */
+/* Composition profile along a cylinder (the atom-probe-like analysis of     */
+/* Sec. 3.2).  Site (x, y, z, b) sits at h = 2*(x,y,z) + basis_b (half      */
+/* units).  Inside: t = (h_axis - o_axis) mod 2n_axis < length, and the sum  */
+/* over the other two axes of d^2, d = (h_d - o_d) mod 2n_d taken in        */
+/* (-n_d, n_d], is <= r2max.  counts[bin * K + sigma] += 1 with              */
+/* bin = t * n_bins / length.                                                */
+/* ------------------------------------------------------------------------ */
+static int64_t mod_pos(int64_t v, int64_t n) {
+  int64_t r = v % n;
+  return r < 0 ? r + n : r;
+}
+
+int orc_profile(const orc_desc *d, const uint8_t *occ, int axis, const int32_t *origin,
+                uint64_t r2max, uint32_t length, uint32_t n_bins, uint64_t *counts) {
+  if (!valid_desc(d) || axis < 0 || axis > 2 || n_bins < 1 || length < 1 ||
+      length > 2u * (uint32_t)d->n[axis])
+    return ORC_EINVAL;
+  memset(counts, 0, sizeof(uint64_t) * n_bins * (size_t)d->K);
+  const int nb = basis_count(d->kind);
+  for (int z = 0; z < d->n[2]; ++z)
+    for (int y = 0; y < d->n[1]; ++y)
+      for (int x = 0; x < d->n[0]; ++x)
+        for (int b = 0; b < nb; ++b) {
+          int bv[3];
+          basis_vec(d->kind, b, bv);
+          const int64_t h[3] = {2 * x + bv[0], 2 * y + bv[1], 2 * z + bv[2]};
+          const int64_t t = mod_pos(h[axis] - origin[axis], 2 * (int64_t)d->n[axis]);
+          if (t >= (int64_t)length) continue;
+          uint64_t r2 = 0;
+          for (int k = 0; k < 3; ++k) {
+            if (k == axis) continue;
+            int64_t dd = mod_pos(h[k] - origin[k], 2 * (int64_t)d->n[k]);
+            if (dd > d->n[k]) dd -= 2 * (int64_t)d->n[k];
+            r2 += (uint64_t)(dd * dd);
+          }
+          if (r2 > r2max) continue;
+          const uint64_t bin = (uint64_t)t * n_bins / length;
+          const uint8_t s = occ[site_index(d, x, y, z, b)];
+          if (s >= d->K) return ORC_EINVAL;
+          counts[bin * (uint64_t)d->K + s] += 1;
+        }
+  return ORC_OK;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Clusters (precipitates, Sec. 3.2): connected components of the sites     */
+/* whose species has its bit set in `mask`, connected through first-shell   */
+/* neighbours (periodic).  Sequential union-find over every first-shell     */
+/* vector of every member site; sizes[0..*n) in descending order.            */
+/* ------------------------------------------------------------------------ */
+static int64_t uf_find(int64_t *par, int64_t x) {
+  int64_t r = x;
+  while (par[r] != r) r = par[r];
+  while (par[x] != r) {
+    const int64_t nx = par[x];
+    par[x] = r;
+    x = nx;
+  }
+  return r;
+}
+
+static int cmp_desc_u64(const void *a, const void *b) {
+  const uint64_t x = *(const uint64_t *)a, y = *(const uint64_t *)b;
+  return x < y ? 1 : (x > y ? -1 : 0);
+}
+
+int orc_clusters(const orc_desc *d, const uint8_t *occ, uint32_t mask, uint64_t *sizes,
+                 uint64_t *n_out) {
+  if (!valid_desc(d)) return ORC_EINVAL;
+  shells_t sh;
+  if (build_shells(d->kind, 1, &sh) != ORC_OK) return ORC_EINVAL;
+  const int64_t N = site_count(d);
+  int64_t *par = (int64_t *)malloc(sizeof(int64_t) * (size_t)N);
+  uint64_t *cnt = (uint64_t *)calloc((size_t)N, sizeof(uint64_t));
+  if (!par || !cnt) {
+    free(par);
+    free(cnt);
+    return ORC_EINVAL;
+  }
+  for (int64_t i = 0; i < N; ++i) par[i] = ((mask >> occ[i]) & 1u) ? i : -1;
+  for (int64_t i = 0; i < N; ++i) {
+    if (par[i] < 0) continue;
+    for (int k = 0; k < sh.z[0]; ++k) {
+      const int64_t j = neighbour(d, i, sh.disp[k]);
+      if (par[j] < 0) continue;
+      const int64_t a = uf_find(par, i), b = uf_find(par, j);
+      if (a != b) par[a < b ? b : a] = a < b ? a : b;
+    }
+  }
+  for (int64_t i = 0; i < N; ++i)
+    if (par[i] >= 0) cnt[uf_find(par, i)] += 1;
+  uint64_t n = 0;
+  for (int64_t i = 0; i < N; ++i)
+    if (cnt[i]) sizes[n++] = cnt[i];
+  qsort(sizes, (size_t)n, sizeof(uint64_t), cmp_desc_u64);
+  *n_out = n;
+  free(par);
+  free(cnt);
+  return ORC_OK;
+}

@@ -135,6 +135,10 @@ SIGNATURES = {
     "smcx_tile_shape": (_st, [ctypes.c_uint32, ctypes.c_uint32, _P(ctypes.c_uint32)]),
     "smcx_kernel_tuning": (_st, [_vp, _P(ctypes.c_uint32), _P(ctypes.c_uint32), _P(ctypes.c_uint32),
                                  _P(ctypes.c_int32), _P(ctypes.c_float)]),
+    "smcx_composition_profile": (_st, [_vp, ctypes.c_uint32, _P(ctypes.c_int32), ctypes.c_uint64,
+                                       ctypes.c_uint32, ctypes.c_uint32, _vp]),
+    "smcx_clusters": (_st, [_vp, ctypes.c_uint32, _vp, ctypes.c_size_t, _P(ctypes.c_uint64), _vp,
+                            ctypes.c_uint64]),
     "smcx_kernel_in_use": (_st, [_vp, _P(ctypes.c_uint32), _P(ctypes.c_int32)]),
     "smcx_destroy": (_st, [_vp]),
     "smcx_last_error": (ctypes.c_char_p, []),

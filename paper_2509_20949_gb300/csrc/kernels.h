@@ -88,3 +88,18 @@ cudaError_t launch_sweep_phase_4(const void* args, uint32_t ph, cudaStream_t st)
 int sweep_queue_blocks_3();
 int sweep_queue_blocks_4();
 }  // namespace smcx
+
+namespace smcx {
+// analyses (analysis.cu): species counts per bin of a cylinder along a
+// lattice axis (counts [n_bins][K], zeroed by the caller; n_bins * K <= 8192)
+cudaError_t launch_profile(const Geom& g, const uint8_t* occ, int axis, const int* origin_h,
+                           unsigned long long r2max, uint32_t length, uint32_t n_bins,
+                           unsigned long long* counts, int n_sm, cudaStream_t st);
+// clusters of the sites with species in `mask` (first-shell connectivity):
+// lab, cnt = n_sites uint32 each (device scratch); afterwards lab[0..*n_out)
+// holds the cluster sizes (any order); *n_out and *err zeroed by the caller,
+// *err != 0 when a capped loop gave up
+cudaError_t launch_clusters(const Geom& g, const uint8_t* occ, uint32_t mask, uint32_t* lab,
+                            uint32_t* cnt, unsigned long long* n_out, unsigned int* err,
+                            uint32_t n_sites, int n_sm, cudaStream_t st);
+}  // namespace smcx

@@ -2,6 +2,7 @@
 // link-cell layout, the per-sweep schedule (origin shift, colours, Metropolis
 // threshold tables) and kernel launches.  Host code only; the kernels live in
 // kernels_*.cu.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -819,6 +820,66 @@ smcx_status smcx_warren_cowley_sro(smcx_lattice* lat, uint32_t n_shells, uint64_
         alpha[(m * K + pc) * K + p] = (n_centre > 0 && n_p > 0) ? 1.0 - cond / conc : NAN;
       }
   }
+  return SMCX_OK;
+}
+
+smcx_status smcx_composition_profile(smcx_lattice* lat, uint32_t axis, const int32_t* origin_h,
+                                     uint64_t radius2_h, uint32_t length_h, uint32_t n_bins,
+                                     uint64_t* counts) {
+  TraceRange trace("smcx_composition_profile");
+  smcx_status s = check_handle(lat);
+  if (s != SMCX_OK) return s;
+  if (axis > 2 || !origin_h || !counts) return fail(SMCX_EINVAL, "bad axis or null argument");
+  const uint64_t K = lat->desc.n_species;
+  if (n_bins < 1 || length_h < 1 || length_h > 2 * lat->desc.n[axis])
+    return fail(SMCX_EINVAL, "need n_bins >= 1 and 1 <= length_h <= 2 n[axis]");
+  if (n_bins * K > 8192 || 8 * n_bins * K > lat->N)
+    return fail(SMCX_EINVAL, "too many bins (n_bins * K <= 8192 and 8 n_bins K <= sites)");
+  const Geom g = lat->geom();
+  auto* d_cnt = reinterpret_cast<unsigned long long*>(lat->scratch());
+  const size_t bytes = sizeof(uint64_t) * n_bins * K;
+  SMCX_CUDA(lat, cudaMemsetAsync(d_cnt, 0, bytes, lat->stream));
+  const int o[3] = {origin_h[0], origin_h[1], origin_h[2]};
+  SMCX_CUDA(lat, launch_profile(g, lat->d_occ, static_cast<int>(axis), o, radius2_h, length_h, n_bins,
+                                d_cnt, lat->n_sm, lat->stream));
+  SMCX_CUDA(lat, cudaMemcpyAsync(counts, d_cnt, bytes, cudaMemcpyDeviceToHost, lat->stream));
+  SMCX_CUDA(lat, cudaStreamSynchronize(lat->stream));
+  return SMCX_OK;
+}
+
+smcx_status smcx_clusters(smcx_lattice* lat, uint32_t species_mask, void* d_scratch,
+                          size_t scratch_bytes, uint64_t* n_clusters, uint64_t* sizes,
+                          uint64_t cap) {
+  TraceRange trace("smcx_clusters");
+  smcx_status s = check_handle(lat);
+  if (s != SMCX_OK) return s;
+  if (!n_clusters || (cap && !sizes)) return fail(SMCX_EINVAL, "null output");
+  if (!d_scratch || scratch_bytes < 8 * lat->N || reinterpret_cast<uintptr_t>(d_scratch) % 16)
+    return fail(SMCX_EINVAL, "scratch must be >= 8 bytes per site and 16-byte aligned");
+  if (lat->N >= 0xFFFFFFFFull) return fail(SMCX_EINVAL, "too many sites for 32-bit labels");
+  const Geom g = lat->geom();
+  auto* lab = static_cast<uint32_t*>(d_scratch);
+  uint32_t* cnt = lab + lat->N;
+  auto* n_out = reinterpret_cast<unsigned long long*>(lat->pairs());
+  auto* err = reinterpret_cast<unsigned int*>(lat->pairs() + 1);
+  SMCX_CUDA(lat, cudaMemsetAsync(lat->pairs(), 0, 16, lat->stream));
+  SMCX_CUDA(lat, launch_clusters(g, lat->d_occ, species_mask, lab, cnt, n_out, err,
+                                 static_cast<uint32_t>(lat->N), lat->n_sm, lat->stream));
+  unsigned long long hdr[2] = {0, 0};
+  SMCX_CUDA(lat, cudaMemcpyAsync(hdr, lat->pairs(), 16, cudaMemcpyDeviceToHost, lat->stream));
+  SMCX_CUDA(lat, cudaStreamSynchronize(lat->stream));
+  if (static_cast<unsigned int>(hdr[1]) != 0) {
+    lat->sticky = SMCX_ETIMEOUT;
+    return fail(SMCX_ETIMEOUT, "cluster labelling: a capped loop gave up");
+  }
+  *n_clusters = hdr[0];
+  if (cap == 0 || hdr[0] == 0) return SMCX_OK;
+  std::vector<uint32_t> all(hdr[0]);
+  SMCX_CUDA(lat, cudaMemcpyAsync(all.data(), lab, sizeof(uint32_t) * all.size(),
+                                 cudaMemcpyDeviceToHost, lat->stream));
+  SMCX_CUDA(lat, cudaStreamSynchronize(lat->stream));
+  std::sort(all.begin(), all.end(), [](uint32_t a, uint32_t b) { return a > b; });
+  for (uint64_t k = 0; k < cap && k < all.size(); ++k) sizes[k] = all[k];
   return SMCX_OK;
 }
 

@@ -170,6 +170,45 @@ class Lattice:
                  for c in range(min(int(n.value), 8))]
         return dict(done=bool(done.value), candidates=cands)
 
+    def composition_profile(self, axis, origin_h, radius2_h, length_h, n_bins):
+        """Species counts [n_bins][K] along a cylinder (see smcx.h); positions
+        in half lattice-constant units."""
+        counts = np.zeros((int(n_bins), self.K), dtype=np.uint64)
+        o = (ctypes.c_int32 * 3)(*[int(v) for v in origin_h])
+        check(self.L.smcx_composition_profile(self.h, int(axis), o, int(radius2_h), int(length_h),
+                                              int(n_bins), _host_ptr(counts)))
+        return counts
+
+    def clusters(self, species, cap=None):
+        """Sizes (descending) of the first-shell-connected clusters of the
+        sites whose species is in `species` (precipitates, Sec. 3.2)."""
+        torch = self._torch
+        mask = 0
+        for sp in species:
+            mask |= 1 << int(sp)
+        scratch = torch.empty(8 * self.N, dtype=torch.uint8, device=self.device)
+        n = ctypes.c_uint64()
+        cap = self.N if cap is None else int(cap)
+        sizes = np.zeros(max(cap, 1), dtype=np.uint64)
+        check(self.L.smcx_clusters(self.h, mask, ctypes.c_void_p(scratch.data_ptr()),
+                                   8 * self.N, ctypes.byref(n), _host_ptr(sizes), cap))
+        return sizes[: min(cap, int(n.value))]
+
+    def sro_average(self, n_shells, n_samples, sweeps_between, T):
+        """Warren-Cowley parameters averaged over configurations (Sec. 3.2,
+        Eq. 9): n_samples snapshots, each after sweeps_between sweeps at T.
+        The species counts are conserved by swaps, so alpha is linear in the
+        pair counts and the average of alpha is alpha of the summed counts.
+        Returns (summed pair counts, mean alpha)."""
+        total = None
+        alphas = []
+        for _ in range(int(n_samples)):
+            self.sweep(int(sweeps_between), float(T), stats=False)
+            cnt, alpha = self.sro(n_shells)
+            total = cnt.copy() if total is None else total + cnt
+            alphas.append(alpha)
+        return total, np.mean(np.stack(alphas), axis=0)
+
     def checkpoint(self) -> bytes:
         n = ctypes.c_size_t()
         check(self.L.smcx_checkpoint(self.h, None, ctypes.byref(n)))
