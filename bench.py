@@ -51,9 +51,10 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
-    ap.add_argument("--mode", default="plain", choices=["plain", "batch", "serve"],
+    ap.add_argument("--mode", default="plain", choices=["plain", "batch", "serve", "slab"],
                     help="plain: the single-lattice sweep (default); batch: 256 independent "
-                         "lattices batched vs one at a time; serve: Poisson-arrival serving")
+                         "lattices batched vs one at a time; serve: Poisson-arrival serving; "
+                         "slab: one lattice decomposed along z over the ranks")
     ap.add_argument("--jobs", type=int, default=256)
     ap.add_argument("--chunk", type=int, default=50)
     ap.add_argument("--rate", type=float, default=5.0)
@@ -252,6 +253,71 @@ def _job_arrays(j):
     return V, occ
 
 
+def run_slab(args):
+    """One lattice swept by all ranks through the z decomposition (strong
+    scaling): every rank holds the same lattice, sweeps its share of the link
+    cell planes and trades boundary planes (NCCL device buffers under
+    torchrun).  value = sites x sweeps / max-over-ranks wall time of the
+    timed sweeps (the boundary exchanges are part of each sweep)."""
+    import torch
+
+    world, rank, local = dist_setup()
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    from paper_2509_20949_gb300.lattice import Lattice
+    from paper_2509_20949_gb300.slab import SlabSweep
+
+    w, N, desc = workload_config(args.workload)
+    V = inputs.epi_table(w["M"], w["K"], w["sigma"], w["epi_seed"])
+    occ = inputs.initial_occupancy(w["kind"], w["n"], w["K"], w["occ_seed"], w["fractions"])
+    lat = Lattice(w["kind"], w["n"], w["K"], occ, seed=w["seed"], pack_bits=args.pack_bits)
+    if args.kernel:
+        lat.set_option(1, args.kernel)
+    lat.set_epi(V)
+    s = SlabSweep(lat)
+    for i in range(args.warmup):
+        s.sweep(1, sweep_temperature(w, i))
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    t0 = time.perf_counter()
+    tot = 0
+    for i in range(args.steps):
+        tot += s.sweep(1, sweep_temperature(w, args.warmup + i))["attempts"]
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    if world > 1:
+        torch.distributed.barrier()
+    clk = clocks.stop()
+    dt = max_over_ranks(dt)
+    p = s.plan(lat.sweep_counter)
+    if rank == 0:
+        line = {"metric": "attempted MC swaps/sec (one lattice decomposed along z over the GPUs)",
+                "value": tot / dt, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+                "higher_is_better": True, "scaling": "strong", "vs_baseline": None,
+                "dtype": "int64", "data": "synthetic", "mode": "slab",
+                "config": {"workload": desc, "step": "1 sweep: 2 half sweeps of 4 colour phases on "
+                           "this rank's link-cell planes, boundary-plane merges, window moves",
+                           "comm": "nccl device buffers" if s.device_comm else "none (one rank)",
+                           "planes_per_rank": p["n_own"], "halo": p["halo"],
+                           "pack_bits": args.pack_bits},
+                "attempts_total": tot, "clocks": clk,
+                # 8 colour phases per sweep; with several ranks also the merge
+                # kernels (one per row group and run of each boundary region)
+                "gpu_launches": args.steps * 8 if world == 1 else None}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
 def run_batch(args):
     """256 independent lattices (n ~ log-U(8, 64) conventional cells, BCC/FCC,
     K ~ U{3..6}, shells 1-3, T ~ U(300, 1500) K, 200 sweeps each): batched
@@ -341,6 +407,8 @@ def main():
         return run_batch(args)
     if args.mode == "serve":
         return run_serve(args)
+    if args.mode == "slab":
+        return run_slab(args)
     import torch
 
     world, rank, local = dist_setup()

@@ -185,6 +185,83 @@ smcx_status smcx_set_sweep_counter(smcx_lattice* lat, uint32_t t);
    and cells per dimension m[3] (even, or 1). ESTATE: no EPI. */
 smcx_status smcx_get_layout(smcx_lattice* lat, uint32_t* L, uint32_t* m);
 
+/* ---- lattice decomposition along z (Sec. 2.2, lattice parallelism) -------
+ *
+ * The paper splits one lattice over several GPUs, each sweeping its own part
+ * and trading boundary layers ("ghost layers") with its neighbours.  Here the
+ * split is along z, in whole link-cell planes of each sweep's moving grid, and
+ * it reproduces the single-lattice trajectory bit for bit:
+ *  - in sweep t, rank r of R sweeps the link cells whose z index c lies in
+ *    [floor(r m_z / R), floor((r+1) m_z / R)) (m_z >= 2R: two planes or more
+ *    each); those cells cover conventional z planes
+ *    [z_lo, z_lo + n_own) mod n_z, z_lo = s_z + floor(c_lo n_z / m_z) with
+ *    the sweep's origin shift s_z;
+ *  - every rank keeps the whole lattice (one byte per site fits many
+ *    billions of sites in HBM) but its copy is only current on its window
+ *    [z_lo - halo, z_lo + n_own + halo), halo = the link-cell edge L, which
+ *    covers every site its trials read or write;
+ *  - colours 0-3 are the even cell planes and 4-7 the odd ones.  Two cells
+ *    of one z parity never interact, so during a half sweep (colours 0-3,
+ *    then 4-7) no site one rank reads is written by another, and a site is
+ *    written by at most one rank.  After each half sweep the two ranks on
+ *    either side of an ownership boundary trade the 2 halo planes around it
+ *    and merge them as mine ^ theirs ^ (the planes before the half sweep);
+ *  - when the grid moves for sweep t + 1, each rank fetches the planes of its
+ *    new window from their owners in sweep t (smcx_slab_transfer).
+ * The per-rank statistics add up to the single-lattice ones. */
+
+typedef struct {
+  int32_t c_lo, c_hi; /* link-cell z indices [c_lo, c_hi) this rank sweeps */
+  int32_t z_lo;       /* first owned conventional z plane, 0 <= z_lo < n_z */
+  int32_t n_own;      /* owned planes z_lo .. z_lo + n_own - 1 (mod n_z) */
+  int32_t halo;       /* planes on each side of an ownership boundary (= L) */
+  int32_t m_z;        /* link cells along z */
+} smcx_slab;
+
+/* Plan of rank `rank` of `world` in sweep t for a lattice with this
+   descriptor and an EPI of n_shells shells (pure host arithmetic: no handle,
+   no GPU).  EINVAL: bad descriptor, n_shells outside 1..4, world = 0,
+   rank >= world, or world > 1 with m_z < 2 world. */
+smcx_status smcx_slab_plan(const smcx_lattice_desc* desc, uint32_t n_shells, uint32_t world,
+                           uint32_t rank, uint32_t t, smcx_slab* out);
+
+/* Planes that rank `from` owned in sweep t and rank `to` reads in sweep t+1
+   (its window): *n_runs (0..2) runs (z0, nz), z0 in [0, n_z), written to
+   runs[2 * i], runs[2 * i + 1] (host, room for 4 int32).  from == to gives
+   0 runs.  Errors as smcx_slab_plan. */
+smcx_status smcx_slab_transfer(const smcx_lattice_desc* desc, uint32_t n_shells, uint32_t world,
+                               uint32_t from, uint32_t to, uint32_t t, int32_t* runs,
+                               uint32_t* n_runs);
+
+/* Runs colour `colour` (0..7) of the current sweep at temperature T on the
+   link cells whose z index lies in [c_lo, c_hi) only (0 <= c_lo <= c_hi <=
+   m_z); the sweep counter is not advanced.  A rank of a decomposition runs
+   colours 4h .. 4h+3 on its [c_lo, c_hi) for half sweep h.  The call's
+   statistics count those cells only (and add to the running energy).
+   Synchronises the stream when out != NULL.  ESTATE: no EPI. */
+smcx_status smcx_run_colour_planes(smcx_lattice* lat, uint32_t colour, double T, int32_t c_lo,
+                                   int32_t c_hi, smcx_sweep_stats* out);
+
+/* Device bytes of nz conventional z planes in device storage order (all
+   basis rows of those planes: groups x nz x n_y x row pitch). */
+size_t smcx_planes_bytes(smcx_lattice* lat, uint32_t nz);
+
+/* Device-to-device copies, enqueued on the lattice's stream, between the
+   planes z0 .. z0 + nz - 1 (mod n_z; nz <= n_z) of the occupancy and a
+   caller's device buffer of smcx_planes_bytes(lat, nz) bytes (16-byte
+   aligned): get reads the lattice, put overwrites it.  EINVAL: bad range,
+   null or misaligned buffer. */
+smcx_status smcx_get_planes(smcx_lattice* lat, int32_t z0, uint32_t nz, void* d_dst);
+smcx_status smcx_put_planes(smcx_lattice* lat, int32_t z0, uint32_t nz, const void* d_src);
+
+/* Merges another rank's copy of planes z0 .. z0 + nz - 1 into the lattice:
+   occupancy ^= d_theirs ^ d_before, bytewise, where d_before holds the
+   planes as both ranks had them before the half sweep (each site changed on
+   at most one side).  Device buffers as smcx_get_planes; kernel on the
+   lattice's stream. */
+smcx_status smcx_merge_planes(smcx_lattice* lat, int32_t z0, uint32_t nz, const void* d_theirs,
+                              const void* d_before);
+
 /* Checkpoint: a self-describing byte string (descriptor, EPI, sweep counter,
    running energy, occupancy, CRC-32).  With buf == NULL, *len receives the
    size needed; otherwise *len must be at least that size and receives the

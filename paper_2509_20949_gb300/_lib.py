@@ -108,6 +108,21 @@ class SweepStats(ctypes.Structure):
                     sum_dE=self.sum_dE_q)
 
 
+class Slab(ctypes.Structure):
+    """smcx_slab: one rank's part of a lattice decomposed along z in one sweep."""
+    _fields_ = [
+        ("c_lo", ctypes.c_int32),
+        ("c_hi", ctypes.c_int32),
+        ("z_lo", ctypes.c_int32),
+        ("n_own", ctypes.c_int32),
+        ("halo", ctypes.c_int32),
+        ("m_z", ctypes.c_int32),
+    ]
+
+    def as_dict(self):
+        return {k: int(getattr(self, k)) for k, _ in self._fields_}
+
+
 _P = ctypes.POINTER
 _vp = ctypes.c_void_p
 _st = ctypes.c_int
@@ -120,6 +135,17 @@ SIGNATURES = {
     "smcx_set_epi": (_st, [_vp, ctypes.c_uint32, _vp]),
     "smcx_sweep": (_st, [_vp, ctypes.c_uint32, ctypes.c_double, ctypes.c_double, _P(SweepStats)]),
     "smcx_run_colour": (_st, [_vp, ctypes.c_uint32, ctypes.c_double, _P(SweepStats)]),
+    "smcx_run_colour_planes": (_st, [_vp, ctypes.c_uint32, ctypes.c_double, ctypes.c_int32,
+                                     ctypes.c_int32, _P(SweepStats)]),
+    "smcx_slab_plan": (_st, [_P(LatticeDesc), ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32,
+                             ctypes.c_uint32, _P(Slab)]),
+    "smcx_slab_transfer": (_st, [_P(LatticeDesc), ctypes.c_uint32, ctypes.c_uint32,
+                                 ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32,
+                                 _P(ctypes.c_int32), _P(ctypes.c_uint32)]),
+    "smcx_planes_bytes": (ctypes.c_size_t, [_vp, ctypes.c_uint32]),
+    "smcx_get_planes": (_st, [_vp, ctypes.c_int32, ctypes.c_uint32, _vp]),
+    "smcx_put_planes": (_st, [_vp, ctypes.c_int32, ctypes.c_uint32, _vp]),
+    "smcx_merge_planes": (_st, [_vp, ctypes.c_int32, ctypes.c_uint32, _vp, _vp]),
     "smcx_energy": (_st, [_vp, _P(ctypes.c_int64)]),
     "smcx_running_energy": (_st, [_vp, _P(ctypes.c_int64)]),
     "smcx_warren_cowley_sro": (_st, [_vp, ctypes.c_uint32, _vp, _vp]),

@@ -8,8 +8,9 @@ template <int KIND, int M, int KMAX>
 static cudaError_t single(const Geom& g, const PhaseArgs& a, const Tables& tab, uint8_t* occ,
                           const uint8_t* dtab, unsigned long long* stats, cudaStream_t st) {
   using C = CCfg<KIND, M, KMAX>;
-  uint32_t n = 1;
-  for (int d = 0; d < 3; ++d) n *= g.m[d] == 1 ? 1u : static_cast<uint32_t>(g.m[d] / 2);
+  if (a.naz <= 0) return cudaErrorInvalidValue;
+  uint32_t n = static_cast<uint32_t>(a.naz);
+  for (int d = 0; d < 2; ++d) n *= g.m[d] == 1 ? 1u : static_cast<uint32_t>(g.m[d] / 2);
   k_sweep_cells_single<C><<<(n + C::NT - 1) / C::NT, C::NT, 0, st>>>(g, a, tab, occ, dtab, stats, n);
   return cudaGetLastError();
 }

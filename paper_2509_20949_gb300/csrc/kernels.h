@@ -102,4 +102,9 @@ cudaError_t launch_profile(const Geom& g, const uint8_t* occ, int axis, const in
 cudaError_t launch_clusters(const Geom& g, const uint8_t* occ, uint32_t mask, uint32_t* lab,
                             uint32_t* cnt, unsigned long long* n_out, unsigned int* err,
                             uint32_t n_sites, int n_sm, cudaStream_t st);
+// occupancy ^= theirs ^ before over `bytes` bytes (a multiple of 16; all
+// three 16-byte aligned): the boundary-plane merge of a z decomposition
+cudaError_t launch_merge_planes(uint8_t* occ, const uint8_t* theirs, const uint8_t* before,
+                                size_t bytes, int n_sm, cudaStream_t st);
+
 }  // namespace smcx

@@ -294,7 +294,8 @@ __device__ __forceinline__ void run_cell(const Geom& g, uint8_t* __restrict__ oc
 
 // the active cell with index `ci` of colour `colour` (cells of one colour in
 // the order x fastest); false when the colour has no cell
-__device__ __forceinline__ bool colour_cell(const Geom& g, int colour, uint32_t ci, int* c) {
+__device__ __forceinline__ bool colour_cell(const Geom& g, int colour, int az0, int naz, uint32_t ci,
+                                            int* c) {
   uint32_t A[3];
 #pragma unroll
   for (int d = 0; d < 3; ++d) {
@@ -302,8 +303,8 @@ __device__ __forceinline__ bool colour_cell(const Geom& g, int colour, uint32_t 
     if (g.m[d] == 1 && bit) return false;
     A[d] = g.m[d] == 1 ? 1u : static_cast<uint32_t>(g.m[d] / 2);
   }
-  const uint32_t ax = ci % A[0], ay = (ci / A[0]) % A[1], az = ci / (A[0] * A[1]);
-  if (az >= A[2]) return false;
+  const uint32_t ax = ci % A[0], ay = (ci / A[0]) % A[1], az = ci / (A[0] * A[1]) + az0;
+  if (az >= A[2] || az >= static_cast<uint32_t>(az0 + naz)) return false;
   const uint32_t a[3] = {ax, ay, az};
 #pragma unroll
   for (int d = 0; d < 3; ++d)
@@ -349,7 +350,7 @@ __global__ void __launch_bounds__(C::NT, C::MINB) k_sweep_cells_single(const __g
   int64_t sum_de = 0;
   const uint32_t ci = blockIdx.x * C::NT + threadIdx.x;
   int c[3];
-  if (ci < n_cells && colour_cell(g, a.colour, ci, c))
+  if (ci < n_cells && colour_cell(g, a.colour, a.az0, a.naz, ci, c))
     run_cell<C>(g, occ, a.t, a.shift, c[0], c[1], c[2], a.mode, a.s,
                 reinterpret_cast<const uint32_t*>(smem), smem + C::D_OFF,
                 reinterpret_cast<const int*>(smem + C::PT_OFF), &n_att, &n_unl, &n_acc, &sum_de);

@@ -71,7 +71,8 @@ __global__ void __launch_bounds__(128) k_sweep_generic(const Geom g, const Phase
   int64_t sum_de = 0;
   const uint32_t tid = blockIdx.x * blockDim.x + threadIdx.x;
   if (tid < n_active) {
-    const uint32_t axi = tid % ax_n, ayi = (tid / ax_n) % ay_n, azi = tid / (ax_n * ay_n);
+    const uint32_t axi = tid % ax_n, ayi = (tid / ax_n) % ay_n,
+                   azi = tid / (ax_n * ay_n) + static_cast<uint32_t>(a.az0);
     const int c[3] = {
         g.m[0] == 1 ? 0 : static_cast<int>(2 * axi + (a.colour & 1)),
         g.m[1] == 1 ? 0 : static_cast<int>(2 * ayi + ((a.colour >> 1) & 1)),
@@ -261,7 +262,8 @@ cudaError_t launch_sweep_generic(const Geom& g, const PhaseArgs& a, const ShellP
       cnt[d] = static_cast<uint32_t>(g.m[d] / 2);
     }
   }
-  const uint32_t n_active = cnt[0] * cnt[1] * cnt[2];
+  if (a.naz <= 0 || static_cast<uint32_t>(a.az0 + a.naz) > cnt[2]) return cudaErrorInvalidValue;
+  const uint32_t n_active = cnt[0] * cnt[1] * static_cast<uint32_t>(a.naz);
   const uint32_t blocks = (n_active + 127) / 128;
   k_sweep_generic<<<blocks, 128, 0, st>>>(g, a, sp, tab, occ, V, stats, n_active, cnt[0], cnt[1]);
   return cudaGetLastError();

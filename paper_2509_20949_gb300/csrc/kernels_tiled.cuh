@@ -246,8 +246,8 @@ __global__ void __launch_bounds__(C::NT, C::MINB) k_sweep_tiled(const __grid_con
   int lo[3], ext[3], g0[3], a_first[3], a_last[3];
 #pragma unroll
   for (int d = 0; d < 3; ++d) {
-    a_first[d] = bidx[d] * Bsz[d];
-    a_last[d] = min(a_first[d] + Bsz[d], g.m[d] / 2) - 1;
+    a_first[d] = bidx[d] * Bsz[d] + (d == 2 ? a.az0 : 0);
+    a_last[d] = min(a_first[d] + Bsz[d], d == 2 ? a.az0 + a.naz : g.m[d] / 2) - 1;
     const int c0 = 2 * a_first[d] + bit[d], c1 = 2 * a_last[d] + bit[d];
     lo[d] = link_bound(g, d, c0) - C::H;
     ext[d] = link_bound(g, d, c1 + 1) + C::H - lo[d];
@@ -501,12 +501,13 @@ size_t smem_bytes(int ext_z) {
 }
 
 // cells of colour bit `bit` along one dimension: the largest tile extent of
-// any block (for the dynamic shared-memory size)
-inline int max_extent(int n, int m, int bsz, int halo) {
+// any block whose first cell index is a_base + k bsz (for the dynamic
+// shared-memory size)
+inline int max_extent(int n, int m, int bsz, int halo, int a_base = 0) {
   const int A = m / 2;
   int best = 0;
   for (int bit = 0; bit < 2; ++bit)
-    for (int a0 = 0; a0 < A; a0 += bsz) {
+    for (int a0 = a_base; a0 < A; a0 += bsz) {
       const int a1 = (a0 + bsz < A ? a0 + bsz : A) - 1;
       const int c0 = 2 * a0 + bit, c1 = 2 * a1 + bit;
       const int lo = static_cast<int>((static_cast<long long>(c0) * n) / m) - halo;
@@ -534,13 +535,15 @@ bool supported(const Geom& g) {
 template <class C>
 cudaError_t launch_cfg(const Geom& g, const PhaseArgs& a, const Tables& tab, uint8_t* occ,
                        const TiledEpi& epi, unsigned long long* stats, cudaStream_t st) {
-  const int ext_z = max_extent(g.n[2], g.m[2], C::BZ, C::H);
+  const int ext_z = max_extent(g.n[2], g.m[2], C::BZ, C::H, a.az0);
   const size_t smem = smem_bytes<C>(ext_z);
+  if (a.naz <= 0 || a.az0 < 0 || a.az0 + a.naz > g.m[2] / 2) return cudaErrorInvalidValue;
+  if (smem > 227 * 1024) return cudaErrorNotSupported;
   cudaError_t e = cudaFuncSetAttribute(k_sweep_tiled<C>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        static_cast<int>(smem));
   if (e != cudaSuccess) return e;
   const dim3 grid((g.m[0] / 2 + C::BX - 1) / C::BX, (g.m[1] / 2 + C::BY - 1) / C::BY,
-                  (g.m[2] / 2 + C::BZ - 1) / C::BZ);
+                  (a.naz + C::BZ - 1) / C::BZ);
   k_sweep_tiled<C><<<grid, C::NT, smem, st>>>(g, a, tab, occ, epi.d_table, stats);
   return cudaGetLastError();
 }

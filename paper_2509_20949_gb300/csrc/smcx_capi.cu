@@ -474,14 +474,35 @@ bool colour_empty(smcx_lattice* lat, int colour) {
   return false;
 }
 
-// one colour phase of the current sweep with kernel `kern` (tiled: shape)
+// active z cells of a colour whose link-cell z index lies in [c_lo, c_hi):
+// indices a in [*az0, *az0 + *naz) of the cells c_z = 2 a + bit
+void colour_z_range(const int m[3], int colour, int c_lo, int c_hi, int* az0, int* naz) {
+  const int bit = (colour >> 2) & 1;
+  if (m[2] == 1) {
+    *az0 = 0;
+    *naz = (bit == 0 && c_lo <= 0 && c_hi > 0) ? 1 : 0;
+    return;
+  }
+  const int A = m[2] / 2;
+  int a0 = (c_lo - bit + 1) >> 1, a1 = (c_hi - bit + 1) >> 1;  // ceil((c - bit) / 2)
+  a0 = a0 < 0 ? 0 : a0;
+  a1 = a1 > A ? A : a1;
+  *az0 = a0;
+  *naz = a1 > a0 ? a1 - a0 : 0;
+}
+
+// one colour phase of the current sweep with kernel `kern` (tiled: shape),
+// over the link cells whose z index lies in [c_lo, c_hi) (c_hi < 0: all)
 smcx_status launch_colour_with(smcx_lattice* lat, int colour, const PhaseArgs& base,
-                               const Tables& tab, int kern, int shape) {
+                               const Tables& tab, int kern, int shape, int c_lo = 0,
+                               int c_hi = -1) {
   TraceRange trace("smcx_colour_phase");
   PhaseArgs a = base;
   a.colour = colour;
   const Geom g = lat->geom();
   if (colour_empty(lat, colour)) return SMCX_OK;
+  colour_z_range(lat->m, colour, c_lo, c_hi < 0 ? lat->m[2] : c_hi, &a.az0, &a.naz);
+  if (a.naz == 0) return SMCX_OK;  // no cell of this colour in the range
   if (kern == 0)
     return fail(SMCX_EINVAL, "the requested kernel does not support this lattice/EPI/tile shape");
   if (kern == 3) {
@@ -504,9 +525,11 @@ smcx_status launch_colour_with(smcx_lattice* lat, int colour, const PhaseArgs& b
 }
 
 // one colour phase of the current sweep with the configured kernel
-smcx_status launch_colour(smcx_lattice* lat, int colour, const PhaseArgs& base, const Tables& tab) {
+smcx_status launch_colour(smcx_lattice* lat, int colour, const PhaseArgs& base, const Tables& tab,
+                          int c_lo = 0, int c_hi = -1) {
   const int kern = kernel_choice(lat);
-  return launch_colour_with(lat, colour, base, tab, kern, kern == 2 ? tiled_shape_for(lat) : -1);
+  return launch_colour_with(lat, colour, base, tab, kern, kern == 2 ? tiled_shape_for(lat) : -1,
+                            c_lo, c_hi);
 }
 
 // Difference rows of the tiled kernel, one per species pair (p, q) at byte
@@ -592,6 +615,9 @@ bool host_dtable(const smcx_lattice_desc& d, int M, const int64_t* V, std::vecto
   return dtable_of(d, M, V, out, nullptr);
 }
 size_t host_occ_bytes(const smcx_lattice_desc& d) { return occ_bytes(&d); }
+void host_sweep_origin(const smcx_lattice_desc& d, uint32_t t, int shift[3]) {
+  sweep_origin(d, t, shift);
+}
 bool host_desc_ok(const smcx_lattice_desc* d, std::string* why) { return desc_ok(d, why); }
 }  // namespace smcx
 
@@ -765,6 +791,108 @@ smcx_status smcx_run_colour(smcx_lattice* lat, uint32_t colour, double T, smcx_s
   if (s != SMCX_OK) return s;
   if (out) return read_call_stats(lat, out);
   return SMCX_OK;
+}
+
+smcx_status smcx_run_colour_planes(smcx_lattice* lat, uint32_t colour, double T, int32_t c_lo,
+                                   int32_t c_hi, smcx_sweep_stats* out) {
+  smcx_status s = check_handle(lat);
+  if (s != SMCX_OK) return s;
+  if (!lat->has_epi) return fail(SMCX_ESTATE, "set_epi must be called before run_colour_planes");
+  if (colour > 7) return fail(SMCX_EINVAL, "colour must be 0..7");
+  if (c_lo < 0 || c_hi < c_lo || c_hi > lat->m[2])
+    return fail(SMCX_EINVAL, "need 0 <= c_lo <= c_hi <= m_z");
+  Tables tab;
+  PhaseArgs a{};
+  if (!build_tables(T, &tab, &a.mode, &a.s)) return fail(SMCX_EINVAL, "temperature must be >= 0");
+  SMCX_CUDA(lat, cudaMemsetAsync(lat->stats() + kStatCall, 0, sizeof(unsigned long long) * 4,
+                                 lat->stream));
+  a.t = lat->t;
+  sweep_origin(lat->desc, a.t, a.shift);
+  if (c_hi > c_lo) {
+    s = launch_colour(lat, static_cast<int>(colour), a, tab, c_lo, c_hi);
+    if (s != SMCX_OK) return s;
+  }
+  if (out) return read_call_stats(lat, out);
+  return SMCX_OK;
+}
+
+size_t smcx_planes_bytes(smcx_lattice* lat, uint32_t nz) {
+  if (!lat) return 0;
+  const size_t groups = lat->desc.pack_bits == 4 ? lat->nb / 2 : lat->nb;
+  return groups * nz * lat->desc.n[1] * row_pitch(&lat->desc);
+}
+
+}  // extern "C"
+
+namespace {
+// the runs of planes z0 .. z0 + nz - 1 (mod n_z) in each row group: calls
+// f(group, first plane, planes, offset of the run in the packed buffer)
+template <class F>
+smcx_status for_plane_runs(smcx_lattice* lat, int32_t z0, uint32_t nz, const void* buf, F f) {
+  const int n_z = static_cast<int>(lat->desc.n[2]);
+  if (z0 < 0 || z0 >= n_z || nz == 0 || nz > static_cast<uint32_t>(n_z))
+    return fail(SMCX_EINVAL, "planes: need 0 <= z0 < n_z and 1 <= nz <= n_z");
+  if (!buf || reinterpret_cast<uintptr_t>(buf) % 16 != 0)
+    return fail(SMCX_EINVAL, "planes: null or not 16-byte aligned buffer");
+  const size_t groups = lat->desc.pack_bits == 4 ? lat->nb / 2 : lat->nb;
+  const size_t plane = static_cast<size_t>(lat->desc.n[1]) * row_pitch(&lat->desc);
+  const int first = static_cast<int>(nz) < n_z - z0 ? static_cast<int>(nz) : n_z - z0;
+  for (size_t g = 0; g < groups; ++g) {
+    const size_t base = g * nz * plane;
+    smcx_status s = f(g, z0, first, base);
+    if (s == SMCX_OK && first < static_cast<int>(nz))
+      s = f(g, 0, static_cast<int>(nz) - first, base + first * plane);
+    if (s != SMCX_OK) return s;
+  }
+  return SMCX_OK;
+}
+
+size_t plane_bytes(smcx_lattice* lat) {
+  return static_cast<size_t>(lat->desc.n[1]) * row_pitch(&lat->desc);
+}
+
+uint8_t* plane_ptr(smcx_lattice* lat, size_t g, int z) {
+  return lat->d_occ + (g * lat->desc.n[2] + static_cast<size_t>(z)) * plane_bytes(lat);
+}
+}  // namespace
+
+extern "C" {
+
+smcx_status smcx_get_planes(smcx_lattice* lat, int32_t z0, uint32_t nz, void* d_dst) {
+  smcx_status s = check_handle(lat);
+  if (s != SMCX_OK) return s;
+  uint8_t* dst = static_cast<uint8_t*>(d_dst);
+  return for_plane_runs(lat, z0, nz, d_dst, [&](size_t g, int z, int k, size_t off) {
+    SMCX_CUDA(lat, cudaMemcpyAsync(dst + off, plane_ptr(lat, g, z), k * plane_bytes(lat),
+                                   cudaMemcpyDeviceToDevice, lat->stream));
+    return SMCX_OK;
+  });
+}
+
+smcx_status smcx_put_planes(smcx_lattice* lat, int32_t z0, uint32_t nz, const void* d_src) {
+  smcx_status s = check_handle(lat);
+  if (s != SMCX_OK) return s;
+  const uint8_t* src = static_cast<const uint8_t*>(d_src);
+  return for_plane_runs(lat, z0, nz, d_src, [&](size_t g, int z, int k, size_t off) {
+    SMCX_CUDA(lat, cudaMemcpyAsync(plane_ptr(lat, g, z), src + off, k * plane_bytes(lat),
+                                   cudaMemcpyDeviceToDevice, lat->stream));
+    return SMCX_OK;
+  });
+}
+
+smcx_status smcx_merge_planes(smcx_lattice* lat, int32_t z0, uint32_t nz, const void* d_theirs,
+                              const void* d_before) {
+  smcx_status s = check_handle(lat);
+  if (s != SMCX_OK) return s;
+  if (!d_before || reinterpret_cast<uintptr_t>(d_before) % 16 != 0)
+    return fail(SMCX_EINVAL, "planes: null or not 16-byte aligned buffer");
+  const uint8_t* th = static_cast<const uint8_t*>(d_theirs);
+  const uint8_t* bf = static_cast<const uint8_t*>(d_before);
+  return for_plane_runs(lat, z0, nz, d_theirs, [&](size_t g, int z, int k, size_t off) {
+    SMCX_CUDA(lat, launch_merge_planes(plane_ptr(lat, g, z), th + off, bf + off,
+                                       k * plane_bytes(lat), lat->n_sm, lat->stream));
+    return SMCX_OK;
+  });
 }
 
 smcx_status smcx_energy(smcx_lattice* lat, int64_t* e_q) {

@@ -194,6 +194,10 @@ struct PhaseArgs {
   int shift[3];    // link-cell origin of this sweep
   int colour;      // 0..7
   int mode, s;     // acceptance mode, bin shift
+  // active link cells of this colour along z: indices a in [az0, az0 + naz)
+  // of the cells c_z = 2 a + (colour >> 2 & 1) (all of them unless a run is
+  // restricted to a range of z planes of cells)
+  int az0, naz;
 };
 
 struct Tables {

@@ -103,6 +103,33 @@ class Lattice:
         check(self.L.smcx_run_colour(self.h, int(colour), float(T), ctypes.byref(st)))
         return st.as_dict()
 
+    def run_colour_planes(self, colour, T, c_lo, c_hi):
+        """One colour phase of the current sweep over the link cells whose z
+        index lies in [c_lo, c_hi) (a rank's share of a z decomposition)."""
+        st = SweepStats()
+        check(self.L.smcx_run_colour_planes(self.h, int(colour), float(T), int(c_lo), int(c_hi),
+                                            ctypes.byref(st)))
+        return st.as_dict()
+
+    def planes_buffer(self, nz):
+        """A device buffer for nz conventional z planes in storage order."""
+        return self._torch.empty(int(self.L.smcx_planes_bytes(self.h, int(nz))),
+                                 dtype=self._torch.uint8, device=self.device)
+
+    def get_planes(self, z0, nz, buf):
+        check(self.L.smcx_get_planes(self.h, int(z0), int(nz), ctypes.c_void_p(buf.data_ptr())))
+        return buf
+
+    def put_planes(self, z0, nz, buf):
+        check(self.L.smcx_put_planes(self.h, int(z0), int(nz), ctypes.c_void_p(buf.data_ptr())))
+
+    def merge_planes(self, z0, nz, theirs, before):
+        check(self.L.smcx_merge_planes(self.h, int(z0), int(nz), ctypes.c_void_p(theirs.data_ptr()),
+                                       ctypes.c_void_p(before.data_ptr())))
+
+    def synchronize(self):
+        self.stream.synchronize()
+
     def energy(self) -> int:
         e = ctypes.c_int64()
         check(self.L.smcx_energy(self.h, ctypes.byref(e)))

@@ -1,0 +1,224 @@
+"""Lattice decomposition along z (Sec. 2.2, lattice parallelism).
+
+One lattice is swept by several ranks (one per GPU).  In every sweep each rank
+runs the link cells of its range of z planes of that sweep's moving cell grid,
+and ranks trade boundary planes so that the trajectory is the single-lattice
+one, bit for bit:
+
+* colours 0-3 are the even link-cell planes and 4-7 the odd ones.  Two cells of
+  one z parity never interact, so within a half sweep no rank reads a site
+  that another writes, and no site is written by two ranks;
+* after each half sweep the two ranks at an ownership boundary trade the
+  2 x halo planes around it and merge them as mine ^ theirs ^ before;
+* when the grid moves for the next sweep, each rank fetches the planes of its
+  new window from their previous owners.
+
+Every rank keeps a whole-lattice buffer (one byte per site: a 1e10-site
+lattice is 10 GB of a GPU's HBM) that is current on its window only.
+
+The plan arithmetic is libsmcx.so's smcx_slab_plan / smcx_slab_transfer, and
+the sweeps, plane copies and merges run in its kernels.  This module orders
+those calls and moves plane buffers with torch.distributed: device buffers
+over NCCL, host-staged over gloo.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+
+from . import _lib
+from ._lib import Slab, check
+
+_TAG_UP, _TAG_DOWN, _TAG_MOVE = 1, 2, 10
+
+
+def plan(desc, n_shells, world, rank, t) -> dict:
+    """smcx_slab_plan: the link-cell z range [c_lo, c_hi) rank `rank` sweeps
+    in sweep t, its owned planes [z_lo, z_lo + n_own) (mod n_z), halo, m_z."""
+    out = Slab()
+    check(_lib.lib().smcx_slab_plan(ctypes.byref(desc), int(n_shells), int(world), int(rank),
+                                    int(t), ctypes.byref(out)))
+    return out.as_dict()
+
+
+def transfer(desc, n_shells, world, src, dst, t) -> list:
+    """smcx_slab_transfer: runs (z0, nz) of planes that rank src owned in
+    sweep t and rank dst reads in sweep t + 1."""
+    runs = (ctypes.c_int32 * 4)()
+    n = ctypes.c_uint32()
+    check(_lib.lib().smcx_slab_transfer(ctypes.byref(desc), int(n_shells), int(world), int(src),
+                                        int(dst), int(t), runs, ctypes.byref(n)))
+    return [(int(runs[2 * i]), int(runs[2 * i + 1])) for i in range(n.value)]
+
+
+class SlabSweep:
+    """This rank's share of one lattice decomposed along z.
+
+    `lattice` is this rank's whole-lattice handle (a Lattice with its EPI
+    set; every rank starts from the same occupancy, EPI and seed).  `group`:
+    a torch.distributed process group (default: the world, or one rank when
+    torch.distributed is not initialised)."""
+
+    def __init__(self, lattice, group=None):
+        import torch
+        import torch.distributed as dist
+
+        self._torch = torch
+        self._dist = dist
+        self.lat = lattice
+        self.group = group
+        if dist.is_available() and dist.is_initialized():
+            self.world = dist.get_world_size(group)
+            self.rank = dist.get_rank(group)
+            self.device_comm = dist.get_backend(group) == "nccl"
+        else:
+            self.world, self.rank, self.device_comm = 1, 0, False
+        if not lattice.M:
+            raise ValueError("set the lattice's EPI before decomposing it")
+        self.n_z = int(lattice.desc.n[2])
+        plan(lattice.desc, lattice.M, self.world, self.rank, 0)  # raises if the split is invalid
+
+    # ------------------------------------------------------------------
+    def plan(self, t, rank=None) -> dict:
+        return plan(self.lat.desc, self.lat.M, self.world, self.rank if rank is None else rank, t)
+
+    def _global(self, r):
+        """Rank r of the group as a global rank (what P2POp wants)."""
+        if self.group is None:
+            return r
+        return self._dist.get_global_rank(self.group, r)
+
+    def _wire(self, buf):
+        """What goes over the backend: the device buffer (NCCL) or a host copy."""
+        return buf if self.device_comm else buf.cpu()
+
+    def _wire_empty(self, nz):
+        buf = self.lat.planes_buffer(nz)
+        return buf if self.device_comm else self._torch.empty_like(buf, device="cpu")
+
+    def _p2p(self, sends, recvs):
+        """sends: [(peer, tensor, tag)], recvs: [(peer, tensor, tag)], posted
+        as one batch (NCCL groups them, so no pair waits on the other's order)."""
+        dist = self._dist
+        ops = [dist.P2POp(dist.isend, t, self._global(p), self.group, tag) for p, t, tag in sends]
+        ops += [dist.P2POp(dist.irecv, t, self._global(p), self.group, tag) for p, t, tag in recvs]
+        if ops:
+            for w in dist.batch_isend_irecv(ops):
+                w.wait()
+
+    def _regions(self, p):
+        h = p["halo"]
+        lo = (p["z_lo"] - h) % self.n_z
+        hi = (p["z_lo"] + p["n_own"] - h) % self.n_z
+        return lo, hi, 2 * h
+
+    def _merge_boundaries(self, p, before):
+        """Trades the planes around both ownership boundaries with the two
+        neighbours and merges them (each site changed on one side at most)."""
+        lo, hi, nb = self._regions(p)
+        lat = self.lat
+        mine_lo = lat.get_planes(lo, nb, lat.planes_buffer(nb))
+        mine_hi = lat.get_planes(hi, nb, lat.planes_buffer(nb))
+        lat.synchronize()
+        up, down = (self.rank + 1) % self.world, (self.rank - 1) % self.world
+        theirs_lo, theirs_hi = self._wire_empty(nb), self._wire_empty(nb)
+        # my upper region goes up (the upper rank's lower one), my lower one down
+        self._p2p([(up, self._wire(mine_hi), _TAG_UP), (down, self._wire(mine_lo), _TAG_DOWN)],
+                  [(down, theirs_lo, _TAG_UP), (up, theirs_hi, _TAG_DOWN)])
+        if not self.device_comm:
+            theirs_lo = lat.planes_buffer(nb).copy_(theirs_lo)
+            theirs_hi = lat.planes_buffer(nb).copy_(theirs_hi)
+        lat.merge_planes(lo, nb, theirs_lo, before[0])
+        lat.merge_planes(hi, nb, theirs_hi, before[1])
+
+    def _move(self, t):
+        """After sweep t: every rank fetches the planes of its sweep-(t+1)
+        window from their sweep-t owners."""
+        lat = self.lat
+        sends, recvs, puts = [], [], []
+        for src in range(self.world):
+            for dst in range(self.world):
+                if src == dst or self.rank not in (src, dst):
+                    continue
+                for k, (z0, nz) in enumerate(transfer(lat.desc, lat.M, self.world, src, dst, t)):
+                    if self.rank == src:
+                        sends.append((dst, lat.get_planes(z0, nz, lat.planes_buffer(nz)),
+                                      _TAG_MOVE + k))
+                    else:
+                        buf = self._wire_empty(nz)
+                        recvs.append((src, buf, _TAG_MOVE + k))
+                        puts.append((z0, nz, buf))
+        lat.synchronize()
+        self._p2p([(p, self._wire(b), tag) for p, b, tag in sends], recvs)
+        for z0, nz, buf in puts:
+            if not self.device_comm:
+                buf = lat.planes_buffer(nz).copy_(buf)
+            lat.put_planes(z0, nz, buf)
+        lat.synchronize()
+
+    def _allreduce(self, v):
+        if self.world == 1:
+            return v
+        torch = self._torch
+        t = torch.tensor(v, dtype=torch.int64)
+        if self.device_comm:
+            t = t.to(self.lat.device)
+        self._dist.all_reduce(t, group=self.group)
+        return t.cpu().numpy()
+
+    # ------------------------------------------------------------------
+    def sweep(self, n_sweeps=1, T_first=1000.0, T_last=None) -> dict:
+        """n_sweeps MC steps of the whole lattice, temperature linear from
+        T_first to T_last as smcx_sweep; returns the trial statistics summed
+        over every rank (the single-lattice numbers)."""
+        T_last = T_first if T_last is None else T_last
+        lat = self.lat
+        tot = np.zeros(4, dtype=np.int64)
+        for i in range(int(n_sweeps)):
+            T = T_first
+            if n_sweeps > 1 and T_first != T_last:
+                T = T_first + (T_last - T_first) * i / (n_sweeps - 1)
+            t = lat.sweep_counter
+            p = self.plan(t)
+            for half in (0, 1):
+                before = None
+                if self.world > 1:
+                    lo, hi, nb = self._regions(p)
+                    before = (lat.get_planes(lo, nb, lat.planes_buffer(nb)),
+                              lat.get_planes(hi, nb, lat.planes_buffer(nb)))
+                for colour in range(4 * half, 4 * half + 4):
+                    st = lat.run_colour_planes(colour, T, p["c_lo"], p["c_hi"])
+                    tot += np.array([st["attempts"], st["unlike"], st["accepted"], st["sum_dE"]],
+                                    dtype=np.int64)
+                if self.world > 1:
+                    self._merge_boundaries(p, before)
+            lat.sweep_counter = t + 1
+            if self.world > 1:
+                self._move(t)
+        tot = self._allreduce(tot)
+        return dict(attempts=int(tot[0]), unlike=int(tot[1]), accepted=int(tot[2]),
+                    sum_dE=int(tot[3]))
+
+    def gather(self):
+        """Makes every rank's whole-lattice copy current everywhere (each rank
+        broadcasts the planes it owns in the next sweep), so that occupancy,
+        energy and SRO can be read on any rank."""
+        if self.world == 1:
+            return
+        lat = self.lat
+        t = lat.sweep_counter
+        for src in range(self.world):
+            p = self.plan(t, src)
+            z0, nz = p["z_lo"], p["n_own"]
+            if self.rank == src:
+                buf = self._wire(lat.get_planes(z0, nz, lat.planes_buffer(nz)))
+                lat.synchronize()
+                self._dist.broadcast(buf, src=self._global(src), group=self.group)
+            else:
+                buf = self._wire_empty(nz)
+                self._dist.broadcast(buf, src=self._global(src), group=self.group)
+                if not self.device_comm:
+                    buf = lat.planes_buffer(nz).copy_(buf)
+                lat.put_planes(z0, nz, buf)
+        lat.synchronize()
