@@ -212,6 +212,9 @@ __device__ __forceinline__ void run_cell(const Geom& g, uint8_t* __restrict__ oc
           J.x[0] = J.x[6] = J.y[0] = J.y[6] = J.z[0] = J.z[6] = 0;
           const uint32_t aj = J.x[3] + J.y[3] + J.z[3] + bofs[bj];
           const uint32_t p = occ[ai], q = occ[aj];
+          // like pairs run the same branch-free path (their result is
+          // discarded): for these L1-cached loads an early exit costs more
+          // in divergence than it saves
           uint32_t acc_i[C::M], acc_j[C::M];
           cacc_i<C, B>(occ, T, bofs, acc_i, std::make_integer_sequence<int, C::M>{});
           if constexpr (C::KIND == 0) {

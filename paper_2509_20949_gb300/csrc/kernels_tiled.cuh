@@ -404,6 +404,11 @@ __global__ void __launch_bounds__(C::NT, C::MINB) k_sweep_tiled(const __grid_con
       const int pt = s_part[B * C::Z1 + dir];
       const int aj = ai + (pt >> 2);
       const uint32_t p = tile[ai], q = tile[aj];
+      // a like pair is a no-op trial (Sec. 2.1): its lanes issue none of the
+      // neighbourhood loads below, which also thins the partner-side bank
+      // conflicts of the lanes that do
+      if (p == q) return;
+      ++n_unl;
       uint32_t acc_i[C::M], acc_j[C::M];
       count_all_i<C, B>(tile + ai, acc_i, std::make_integer_sequence<int, C::M>{});
       if constexpr (C::KIND == 0) {
@@ -419,8 +424,6 @@ __global__ void __launch_bounds__(C::NT, C::MINB) k_sweep_tiled(const __grid_con
         }
         count_all_j_fcc<C>(cls_base, acc_j, std::make_integer_sequence<int, C::M>{});
       }
-      const bool unlike = p != q;
-      n_unl += unlike;
       const uint8_t* row = s_d + (p * C::KMAX + q) * C::RSTEP;
       constexpr int ND = C::M * (C::KMAX - 1);
       int32_t dr[(ND + 3) / 4 * 4];
@@ -455,8 +458,8 @@ __global__ void __launch_bounds__(C::NT, C::MINB) k_sweep_tiled(const __grid_con
       const uint32_t i2 = idx >> 18 < 511u ? static_cast<uint32_t>(idx >> 18) : 511u;
       const uint32_t thr = compose_threshold(s_tab[idx & 511u], s_tab[512 + ((idx >> 9) & 511u)],
                                              s_tab[1024 + i2]);
-      const bool ok = unlike && (de <= 0 || a.mode == kModeAcceptAll ||
-                                 (a.mode == kModeNormal && idx < (1ull << 27) && wb < thr));
+      const bool ok = de <= 0 || a.mode == kModeAcceptAll ||
+                      (a.mode == kModeNormal && idx < (1ull << 27) && wb < thr);
       if (ok) {
         tile[ai] = static_cast<uint8_t>(q);
         tile[aj] = static_cast<uint8_t>(p);
