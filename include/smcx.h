@@ -102,9 +102,8 @@ smcx_status smcx_create_lattice(const smcx_lattice_desc* desc, void* d_occ, void
    in q units, symmetric in the species indices; n_shells in 1..4.  The link
    cells are sized from the shells (edge L = floor((1 + h_R)/2) + 1
    conventional cells, h_R the largest |component| of a shell vector, raised
-   to min_cell).  Computes the full energy, which starts the running energy.
-   EINVAL: n_shells out of range, asymmetric V.  EOVERFLOW: the energy does
-   not fit int64. */
+   to min_cell).  Restarts the running energy (see smcx_running_energy).
+   EINVAL: n_shells out of range, asymmetric V or a value beyond 2^52 q. */
 smcx_status smcx_set_epi(smcx_lattice* lat, uint32_t n_shells, const int64_t* v_q);
 
 /* Runs n_sweeps MC steps (one trial per site each, Sec. 2.1) on the stream.
@@ -130,8 +129,12 @@ smcx_status smcx_run_colour(smcx_lattice* lat, uint32_t colour, double T, smcx_s
    fit int64.  ESTATE: no EPI. */
 smcx_status smcx_energy(smcx_lattice* lat, int64_t* e_q);
 
-/* Running energy: the energy at smcx_set_epi / smcx_set_occupancy plus the
-   sum of every accepted energy change since (no device work). */
+/* Running energy: the energy at the last restart (smcx_set_epi,
+   smcx_set_occupancy, smcx_restore) plus the exact sum of every accepted
+   energy change since.  The base is computed on the first call after a
+   restart, as the full energy at that time minus the accepted changes so far
+   (equal by the incremental identity); later calls only read the device sum.
+   Synchronises.  EOVERFLOW: the full energy does not fit int64. */
 smcx_status smcx_running_energy(smcx_lattice* lat, int64_t* e_q);
 
 /* Warren-Cowley SRO, Sec. 3.2, Eq. 9.  pair_counts (host, required) receives
@@ -146,9 +149,9 @@ smcx_status smcx_warren_cowley_sro(smcx_lattice* lat, uint32_t n_shells, uint64_
 /* Copies the occupancy to h_out (N bytes, canonical layout).  Synchronises. */
 smcx_status smcx_get_occupancy(smcx_lattice* lat, uint8_t* h_out);
 
-/* Replaces the occupancy by h_in (N bytes, canonical, ids < K) and, when an
-   EPI is set, restarts the running energy from its full recomputation.  The
-   sweep counter is unchanged.  Synchronises. */
+/* Replaces the occupancy by h_in (N bytes, canonical, ids < K, validated on
+   the device; on EINVAL the occupancy is left as it was) and restarts the
+   running energy.  The sweep counter is unchanged.  Synchronises. */
 smcx_status smcx_set_occupancy(smcx_lattice* lat, const uint8_t* h_in);
 
 /* Composition profile along a cylinder (the atom-probe-like analysis of

@@ -13,8 +13,10 @@ cudaError_t launch_pair_count_generic(const Geom& g, const ShellParam& sp, int n
                                       const uint8_t* occ, unsigned long long* counts,
                                       uint32_t n_cells, int n_sm, cudaStream_t st);
 
+// (skip: device flag; the conversion does nothing when it is non-zero)
 cudaError_t launch_canon_to_dev(const Geom& g, const uint8_t* canon, uint8_t* occ,
-                                uint32_t n_cells, int n_sm, cudaStream_t st);
+                                uint32_t n_cells, int n_sm, cudaStream_t st,
+                                const unsigned int* skip = nullptr);
 cudaError_t launch_dev_to_canon(const Geom& g, const uint8_t* occ, uint8_t* canon,
                                 uint32_t n_cells, int n_sm, cudaStream_t st);
 cudaError_t launch_validate(const uint8_t* canon, uint64_t n, uint32_t K, unsigned int* flag,

@@ -4,6 +4,7 @@
 // device storage.  In the sweep, one thread runs all trials of one link cell
 // of the active colour (Sec. 2.2: cells of one colour never interact);
 // every neighbour is located from coordinates with periodic wrap.
+#include <type_traits>
 #include "device_util.cuh"
 #include "kernels.h"
 
@@ -194,52 +195,95 @@ __global__ void __launch_bounds__(256) k_pair_count_generic(const Geom g, const 
       if (s_cnt[c]) atomicAdd(&counts[c], static_cast<unsigned long long>(s_cnt[c]));
 }
 
-// canonical bytes -> device storage; one thread per conventional cell
-__global__ void k_canon_to_dev(const Geom g, const uint8_t* __restrict__ canon,
-                               uint8_t* __restrict__ occ, uint32_t n_cells) {
-  for (uint32_t cell = blockIdx.x * blockDim.x + threadIdx.x; cell < n_cells;
-       cell += gridDim.x * blockDim.x) {
-    const int x = static_cast<int>(cell % g.n[0]);
-    const int y = static_cast<int>((cell / g.n[0]) % g.n[1]);
-    const int z = static_cast<int>(cell / (static_cast<uint32_t>(g.n[0]) * g.n[1]));
-    const uint8_t* src = canon + static_cast<size_t>(cell) * g.nb;
-    if (!g.pack4) {
-      for (int b = 0; b < g.nb; ++b) occ[dev_row(g, b, z, y) + x] = static_cast<uint8_t>(src[b] * g.W);
-    } else {
-      for (int b = 0; b < g.nb; b += 2)
-        occ[dev_row(g, b >> 1, z, y) + x] = static_cast<uint8_t>(src[b] | (src[b + 1] << 4));
-    }
-  }
-}
+// Layout conversions.  Canonical row r = z n_y + y holds n_x cells of nb
+// bytes; the device row of group grp of that (z, y) starts at
+// (grp * n_y n_z + r) * px (dev_row).  Blocks stride over rows and threads
+// over x, so there is no per-cell division; one load or store of nb bytes per
+// cell on the canonical side, one byte per group on the device side.
 
-__global__ void k_dev_to_canon(const Geom g, const uint8_t* __restrict__ occ,
-                               uint8_t* __restrict__ canon, uint32_t n_cells) {
-  for (uint32_t cell = blockIdx.x * blockDim.x + threadIdx.x; cell < n_cells;
-       cell += gridDim.x * blockDim.x) {
-    const int x = static_cast<int>(cell % g.n[0]);
-    const int y = static_cast<int>((cell / g.n[0]) % g.n[1]);
-    const int z = static_cast<int>(cell / (static_cast<uint32_t>(g.n[0]) * g.n[1]));
-    uint8_t* dst = canon + static_cast<size_t>(cell) * g.nb;
-    if (!g.pack4) {
-      for (int b = 0; b < g.nb; ++b) dst[b] = static_cast<uint8_t>(occ[dev_row(g, b, z, y) + x] / g.W);
-    } else {
-      for (int b = 0; b < g.nb; b += 2) {
-        const uint8_t v = occ[dev_row(g, b >> 1, z, y) + x];
-        dst[b] = v & 15;
-        dst[b + 1] = v >> 4;
+// canonical -> device storage (codes sigma * W, or two 4-bit ids per byte);
+// writes the row padding [n_x, px) as zeros.  Returns at once when *skip is
+// non-zero (the validation of this upload failed).
+template <int NB, bool PACK4>
+__global__ void k_canon_to_dev(const Geom g, const uint8_t* __restrict__ canon,
+                               uint8_t* __restrict__ occ, const unsigned int* __restrict__ skip) {
+  if (skip && *skip) return;
+  using Cell = typename std::conditional<NB == 2, uint16_t, uint32_t>::type;
+  const uint32_t rows = static_cast<uint32_t>(g.n[1]) * g.n[2];
+  const int nx = g.n[0], px = g.px;
+  const uint32_t W = static_cast<uint32_t>(g.W);
+  for (uint32_t r = blockIdx.x; r < rows; r += gridDim.x) {
+    const Cell* src = reinterpret_cast<const Cell*>(canon + static_cast<size_t>(r) * nx * NB);
+    for (int x = threadIdx.x; x < px; x += blockDim.x) {
+      const uint32_t c = x < nx ? static_cast<uint32_t>(src[x]) : 0u;
+      if constexpr (!PACK4) {
+#pragma unroll
+        for (int b = 0; b < NB; ++b)
+          occ[(static_cast<size_t>(b) * rows + r) * px + x] =
+              static_cast<uint8_t>(((c >> (8 * b)) & 0xFFu) * W);
+      } else {
+#pragma unroll
+        for (int b = 0; b < NB; b += 2)
+          occ[(static_cast<size_t>(b >> 1) * rows + r) * px + x] =
+              static_cast<uint8_t>(((c >> (8 * b)) & 0x0Fu) | (((c >> (8 * b + 8)) & 0x0Fu) << 4));
       }
     }
   }
 }
 
-// flags[0] |= 1 when a canonical byte is >= K
+// device storage -> canonical.  Codes are sigma * W <= 255, so sigma =
+// (code * ceil(2^16 / W)) >> 16 exactly (the rounding error is sigma * e / 2^16
+// with e < W).
+template <int NB, bool PACK4>
+__global__ void k_dev_to_canon(const Geom g, const uint8_t* __restrict__ occ,
+                               uint8_t* __restrict__ canon) {
+  using Cell = typename std::conditional<NB == 2, uint16_t, uint32_t>::type;
+  const uint32_t rows = static_cast<uint32_t>(g.n[1]) * g.n[2];
+  const int nx = g.n[0], px = g.px;
+  const uint32_t inv = (65536u + static_cast<uint32_t>(g.W) - 1u) / static_cast<uint32_t>(g.W);
+  for (uint32_t r = blockIdx.x; r < rows; r += gridDim.x) {
+    Cell* dst = reinterpret_cast<Cell*>(canon + static_cast<size_t>(r) * nx * NB);
+    for (int x = threadIdx.x; x < nx; x += blockDim.x) {
+      uint32_t c = 0;
+      if constexpr (!PACK4) {
+#pragma unroll
+        for (int b = 0; b < NB; ++b) {
+          const uint32_t code = occ[(static_cast<size_t>(b) * rows + r) * px + x];
+          c |= ((code * inv) >> 16) << (8 * b);
+        }
+      } else {
+#pragma unroll
+        for (int b = 0; b < NB; b += 2) {
+          const uint32_t v = occ[(static_cast<size_t>(b >> 1) * rows + r) * px + x];
+          c |= ((v & 0x0Fu) << (8 * b)) | ((v >> 4) << (8 * b + 8));
+        }
+      }
+      dst[x] = static_cast<Cell>(c);
+    }
+  }
+}
+
+// flag[0] |= 1 when a canonical byte is >= K: 16 bytes per thread, bytewise
+// compare of four bytes per word (__vcmpgeu4); the unaligned head and the
+// tail bytewise
 __global__ void k_validate(const uint8_t* __restrict__ canon, uint64_t n, uint32_t K,
                            unsigned int* __restrict__ flag) {
-  bool bad = false;
-  for (uint64_t i = blockIdx.x * static_cast<uint64_t>(blockDim.x) + threadIdx.x; i < n;
-       i += static_cast<uint64_t>(gridDim.x) * blockDim.x)
-    bad |= canon[i] >= K;
-  if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(flag, 1u);
+  const uint64_t head = (16u - (reinterpret_cast<uintptr_t>(canon) & 15u)) & 15u;
+  const uint64_t h = head < n ? head : n;
+  const uint64_t n16 = (n - h) / 16;
+  const uint4* body = reinterpret_cast<const uint4*>(canon + h);
+  const uint32_t k4 = (K > 255u ? 255u : K) * 0x01010101u;
+  const uint64_t tid = blockIdx.x * static_cast<uint64_t>(blockDim.x) + threadIdx.x;
+  const uint64_t stride = static_cast<uint64_t>(gridDim.x) * blockDim.x;
+  uint32_t bad = 0;
+  for (uint64_t i = tid; i < n16; i += stride) {
+    const uint4 v = body[i];
+    bad |= __vcmpgeu4(v.x, k4) | __vcmpgeu4(v.y, k4) | __vcmpgeu4(v.z, k4) | __vcmpgeu4(v.w, k4);
+  }
+  if (K > 255u) bad = 0;  // every byte is a valid id
+  for (uint64_t i = tid; i < h; i += stride) bad |= canon[i] >= K;
+  for (uint64_t i = h + 16 * n16 + tid; i < n; i += stride) bad |= canon[i] >= K;
+  if (__any_sync(0xffffffffu, bad != 0) && (threadIdx.x & 31) == 0) atomicOr(flag, 1u);
 }
 
 static uint32_t grid_for(uint64_t work, int threads, int n_sm) {
@@ -280,20 +324,39 @@ cudaError_t launch_pair_count_generic(const Geom& g, const ShellParam& sp, int n
 }
 
 cudaError_t launch_canon_to_dev(const Geom& g, const uint8_t* canon, uint8_t* occ,
-                                uint32_t n_cells, int n_sm, cudaStream_t st) {
-  k_canon_to_dev<<<grid_for(n_cells, 256, n_sm), 256, 0, st>>>(g, canon, occ, n_cells);
+                                uint32_t n_cells, int n_sm, cudaStream_t st,
+                                const unsigned int* skip) {
+  (void)n_cells;
+  const uint32_t rows = static_cast<uint32_t>(g.n[1]) * g.n[2];
+  const uint32_t blocks = grid_for(rows, 1, n_sm);
+  if (g.nb == 2) {
+    if (g.pack4) k_canon_to_dev<2, true><<<blocks, 256, 0, st>>>(g, canon, occ, skip);
+    else k_canon_to_dev<2, false><<<blocks, 256, 0, st>>>(g, canon, occ, skip);
+  } else {
+    if (g.pack4) k_canon_to_dev<4, true><<<blocks, 256, 0, st>>>(g, canon, occ, skip);
+    else k_canon_to_dev<4, false><<<blocks, 256, 0, st>>>(g, canon, occ, skip);
+  }
   return cudaGetLastError();
 }
 
 cudaError_t launch_dev_to_canon(const Geom& g, const uint8_t* occ, uint8_t* canon,
                                 uint32_t n_cells, int n_sm, cudaStream_t st) {
-  k_dev_to_canon<<<grid_for(n_cells, 256, n_sm), 256, 0, st>>>(g, occ, canon, n_cells);
+  (void)n_cells;
+  const uint32_t rows = static_cast<uint32_t>(g.n[1]) * g.n[2];
+  const uint32_t blocks = grid_for(rows, 1, n_sm);
+  if (g.nb == 2) {
+    if (g.pack4) k_dev_to_canon<2, true><<<blocks, 256, 0, st>>>(g, occ, canon);
+    else k_dev_to_canon<2, false><<<blocks, 256, 0, st>>>(g, occ, canon);
+  } else {
+    if (g.pack4) k_dev_to_canon<4, true><<<blocks, 256, 0, st>>>(g, occ, canon);
+    else k_dev_to_canon<4, false><<<blocks, 256, 0, st>>>(g, occ, canon);
+  }
   return cudaGetLastError();
 }
 
 cudaError_t launch_validate(const uint8_t* canon, uint64_t n, uint32_t K, unsigned int* flag,
                             int n_sm, cudaStream_t st) {
-  k_validate<<<grid_for(n, 256, n_sm), 256, 0, st>>>(canon, n, K, flag);
+  k_validate<<<grid_for((n + 15) / 16, 256, n_sm), 256, 0, st>>>(canon, n, K, flag);
   return cudaGetLastError();
 }
 

@@ -636,9 +636,7 @@ smcx_status smcx_batch_add(smcx_batch* b, const smcx_lattice_desc* desc, const u
   if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
   if (e != cudaSuccess) return fail_release(bcuda(b, e, "batch upload"));
   if (bad) return fail_release(batch_fail(SMCX_EINVAL, "species id >= n_species in occupancy"));
-  e = cudaMemsetAsync(b->at(j.occ_off), 0, ob, b->stream);
-  if (e == cudaSuccess)
-    e = launch_canon_to_dev(j.g, b->scratch(), b->at(j.occ_off), static_cast<uint32_t>(N / j.g.nb),
+  e = launch_canon_to_dev(j.g, b->scratch(), b->at(j.occ_off), static_cast<uint32_t>(N / j.g.nb),
                             b->n_sm, b->stream);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(b->at(b->cl.tabs) + kTabBytes * slot, tab.w, kTabBytes,

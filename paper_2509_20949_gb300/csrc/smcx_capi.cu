@@ -187,7 +187,8 @@ struct smcx_lattice {
   int L = 0;
   int m[3] = {1, 1, 1};
   uint32_t t = 0;
-  int64_t E0 = 0;  // energy when the running energy was last restarted
+  int64_t E0 = 0;         // energy when the running energy was last restarted
+  bool e0_known = false;  // E0 is found on first request: E(now) - sum of accepted dE since
   smcx_status sticky = SMCX_OK;
   int opt_kernel = 0;
   int opt_tile = -1;
@@ -330,15 +331,15 @@ smcx_status upload_occupancy(smcx_lattice* lat, const uint8_t* h) {
   SMCX_CUDA(lat, cudaMemsetAsync(lat->flag(), 0, sizeof(unsigned int), lat->stream));
   SMCX_CUDA(lat, launch_validate(lat->scratch(), lat->N, lat->desc.n_species, lat->flag(),
                                  lat->n_sm, lat->stream));
+  // the conversion skips itself when the validation flagged a byte, so an
+  // invalid upload leaves the lattice as it was
+  SMCX_CUDA(lat, launch_canon_to_dev(g, lat->scratch(), lat->d_occ, n_cells, lat->n_sm,
+                                     lat->stream, lat->flag()));
   unsigned int bad = 0;
   SMCX_CUDA(lat, cudaMemcpyAsync(&bad, lat->flag(), sizeof(bad), cudaMemcpyDeviceToHost,
                                  lat->stream));
   SMCX_CUDA(lat, cudaStreamSynchronize(lat->stream));
   if (bad) return fail(SMCX_EINVAL, "species id >= n_species in occupancy");
-  SMCX_CUDA(lat, cudaMemsetAsync(lat->d_occ, 0, occ_bytes(&lat->desc), lat->stream));
-  SMCX_CUDA(lat, launch_canon_to_dev(g, lat->scratch(), lat->d_occ, n_cells, lat->n_sm,
-                                     lat->stream));
-  SMCX_CUDA(lat, cudaStreamSynchronize(lat->stream));
   return SMCX_OK;
 }
 
@@ -413,10 +414,14 @@ smcx_status full_energy(smcx_lattice* lat, int64_t* e) {
   return energy_from_counts(lat, cnt, e);
 }
 
+// Restarts the running energy: the accepted-dE sums start again from zero.
+// Its base E0 (the energy now) is computed when first asked for, as the full
+// energy at that time minus the exact int64 sum of the dE accepted since:
+// no pair count on every occupancy upload.
 smcx_status restart_running_energy(smcx_lattice* lat) {
   SMCX_CUDA(lat, cudaMemsetAsync(lat->stats(), 0, sizeof(unsigned long long) * 16, lat->stream));
-  if (!lat->has_epi) return SMCX_OK;
-  return full_energy(lat, &lat->E0);
+  lat->e0_known = false;
+  return SMCX_OK;
 }
 
 // tile shape the tiled kernel uses (-1 if it cannot run the lattice)
@@ -908,11 +913,20 @@ smcx_status smcx_running_energy(smcx_lattice* lat, int64_t* e_q) {
   if (s != SMCX_OK) return s;
   if (!lat->has_epi) return fail(SMCX_ESTATE, "no EPI set");
   if (!e_q) return fail(SMCX_EINVAL, "null output");
+  int64_t e_now = 0;
+  if (!lat->e0_known) {
+    s = full_energy(lat, &e_now);
+    if (s != SMCX_OK) return s;
+  }
   unsigned long long cum_de = 0;
   SMCX_CUDA(lat, cudaMemcpyAsync(&cum_de, lat->stats() + kStatCum + 3, sizeof(cum_de),
                                  cudaMemcpyDeviceToHost, lat->stream));
   SMCX_CUDA(lat, cudaStreamSynchronize(lat->stream));
-  *e_q = lat->E0 + static_cast<int64_t>(cum_de);
+  if (!lat->e0_known) {
+    lat->E0 = static_cast<int64_t>(static_cast<uint64_t>(e_now) - cum_de);
+    lat->e0_known = true;
+  }
+  *e_q = static_cast<int64_t>(static_cast<uint64_t>(lat->E0) + cum_de);
   return SMCX_OK;
 }
 
@@ -1132,6 +1146,7 @@ smcx_status smcx_restore(smcx_lattice* lat, const void* buf, size_t len) {
   SMCX_CUDA(lat, cudaMemsetAsync(lat->stats(), 0, sizeof(unsigned long long) * 16, lat->stream));
   SMCX_CUDA(lat, cudaStreamSynchronize(lat->stream));
   lat->E0 = e_run;
+  lat->e0_known = true;
   lat->t = t;
   return SMCX_OK;
 }

@@ -142,3 +142,33 @@ def test_occupancy_into_caller_buffer():
     assert got.ctypes.data == pinned.data_ptr() and np.array_equal(pinned.numpy(), ref)
     with pytest.raises(ValueError):
         lat.occupancy(out=np.empty(lat.N - 1, dtype=np.uint8))
+
+
+@pytest.mark.parametrize("kind,n,K,pack", [(0, (13, 7, 9), 5, 8), (1, (5, 11, 6), 6, 8),
+                                           (0, (9, 6, 10), 3, 4), (1, (7, 5, 4), 4, 4)])
+def test_upload_rejects_bad_ids_and_keeps_the_lattice(orc, kind, n, K, pack):
+    """A species id >= K anywhere (head, body or tail of the flat upload)
+    raises and leaves the occupancy, and the running energy, as they were; a
+    good upload round-trips through the device layout (odd row lengths, both
+    storage widths); the running energy's base, taken on first request, equals
+    the full energy."""
+    require_cuda()
+    from paper_2509_20949_gb300 import SmcxError
+    case = make_case(kind, n, K, 3, seed=12)
+    lat = gpu_lattice(case, pack_bits=pack)
+    lat.sweep(3, 800.0)
+    before = lat.occupancy()
+    e_run = lat.running_energy()
+    assert e_run == lat.energy() == orc.energy(oracle_desc(orc, case), case["V"], before)
+    for pos in (0, 7, lat.N // 2 + 3, lat.N - 1):
+        bad = before.copy()
+        bad[pos] = K
+        with pytest.raises(SmcxError):
+            lat.set_occupancy(bad)
+        assert np.array_equal(lat.occupancy(), before)
+        assert lat.running_energy() == e_run
+    other = make_case(kind, n, K, 3, occ_seed=99)["occ"]
+    lat.set_occupancy(other)
+    assert np.array_equal(lat.occupancy(), other)
+    lat.sweep(2, 600.0)
+    assert lat.running_energy() == lat.energy()
