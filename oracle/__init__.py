@@ -127,6 +127,18 @@ def _load():
             lib.orc_clusters.argtypes = [P(_Desc), P(ctypes.c_uint8), ctypes.c_uint32,
                                          P(ctypes.c_uint64), P(ctypes.c_uint64)]
             lib.orc_clusters.restype = ctypes.c_int
+            lib.orc_local_width.argtypes = [ctypes.c_int, ctypes.c_int]
+            lib.orc_local_energy.argtypes = [P(_Desc), P(ctypes.c_int64), P(ctypes.c_uint8),
+                                             P(ctypes.c_int64)]
+            lib.orc_local_delta_e.argtypes = [P(_Desc), P(ctypes.c_int64), P(ctypes.c_uint8),
+                                              ctypes.c_int64, ctypes.c_int64, P(ctypes.c_int64)]
+            lib.orc_local_layout.argtypes = [P(_Desc), P(ctypes.c_int32), P(ctypes.c_int32)]
+            lib.orc_local_sweeps.argtypes = [P(_Desc), P(ctypes.c_int64), P(ctypes.c_uint8),
+                                             ctypes.c_uint32, ctypes.c_uint32, ctypes.c_double,
+                                             ctypes.c_double, P(_Stats), P(_Opts)]
+            for name in ("orc_local_width", "orc_local_energy", "orc_local_delta_e",
+                         "orc_local_layout", "orc_local_sweeps"):
+                getattr(lib, name).restype = ctypes.c_int
             for name in ("orc_shells", "orc_layout", "orc_thresholds", "orc_energy",
                          "orc_pair_counts", "orc_sro_alpha", "orc_delta_e", "orc_sweeps",
                          "orc_phase_cells"):
@@ -352,3 +364,64 @@ def clusters(desc: Desc, occ, species) -> np.ndarray:
     _check(lib.orc_clusters(ctypes.byref(desc.c()), _ptr(o, ctypes.c_uint8), mask,
                             _ptr(sizes, ctypes.c_uint64), ctypes.byref(n)), "clusters")
     return sizes[: int(n.value)]
+
+
+# ---- local-energy model (the nonlinear short-range model of Sec. 3) ---------
+
+def local_width(kind: int, M: int) -> int:
+    """Length zt of the count axis of a local-energy table: 1 + max z_m."""
+    w = _load().orc_local_width(int(kind), int(M))
+    if w < 0:
+        raise OracleError("local_width: bad kind or M")
+    return w
+
+
+def _T(T):
+    return np.ascontiguousarray(T, dtype=np.int64)
+
+
+def local_energy(desc: Desc, T, occ) -> int:
+    """E = sum_i sum_m sum_s T[m][s_i][s][c_{i,m,s}]."""
+    lib = _load()
+    t, o = _T(T), _occ(occ)
+    e = ctypes.c_int64()
+    _check(lib.orc_local_energy(ctypes.byref(desc.c()), _ptr(t, ctypes.c_int64),
+                                _ptr(o, ctypes.c_uint8), ctypes.byref(e)), "local_energy")
+    return int(e.value)
+
+
+def local_delta_e(desc: Desc, T, occ, i: int, j: int) -> int:
+    lib = _load()
+    t, o = _T(T), _occ(occ)
+    e = ctypes.c_int64()
+    _check(lib.orc_local_delta_e(ctypes.byref(desc.c()), _ptr(t, ctypes.c_int64),
+                                 _ptr(o, ctypes.c_uint8), int(i), int(j), ctypes.byref(e)),
+           "local_delta_e")
+    return int(e.value)
+
+
+def local_layout(desc: Desc):
+    lib = _load()
+    L = ctypes.c_int32()
+    m = np.zeros(3, dtype=np.int32)
+    _check(lib.orc_local_layout(ctypes.byref(desc.c()), ctypes.byref(L), _ptr(m, ctypes.c_int32)),
+           "local_layout")
+    return int(L.value), tuple(int(v) for v in m)
+
+
+def local_sweeps(desc: Desc, T, occ, t0: int, n_sweeps: int, T_first: float, T_last=None,
+                 L_override: int = 0, shuffle_cells: bool = False, shuffle_seed: int = 0):
+    """n_sweeps MC steps of the local-energy model on a copy of occ.
+    Returns (occ_after, per_sweep_stats structured array)."""
+    lib = _load()
+    o = np.array(occ, dtype=np.uint8, copy=True, order="C")
+    t = _T(T)
+    stats = np.zeros(n_sweeps, dtype=STATS_DTYPE)
+    opts = _Opts()
+    opts.L_override, opts.shuffle_cells, opts.shuffle_seed = int(L_override), int(bool(shuffle_cells)), int(shuffle_seed)
+    T_last = T_first if T_last is None else T_last
+    code = lib.orc_local_sweeps(ctypes.byref(desc.c()), _ptr(t, ctypes.c_int64), _ptr(o, ctypes.c_uint8),
+                                int(t0), int(n_sweeps), float(T_first), float(T_last),
+                                stats.ctypes.data_as(ctypes.POINTER(_Stats)), ctypes.byref(opts))
+    _check(code, "local_sweeps")
+    return o, stats

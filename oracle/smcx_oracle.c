@@ -443,14 +443,17 @@ typedef struct {
   int m[3];
 } layout_t;
 
-static int compute_layout(const orc_desc *d, const shells_t *sh, int L_override, layout_t *lay) {
+static int compute_layout(const orc_desc *d, const shells_t *sh, int L_override, layout_t *lay,
+                          int local) {
   int hR = 0;
   for (int t = 0; t < sh->total; ++t)
     for (int c = 0; c < 3; ++c) {
       int a = abs(sh->disp[t][c]);
       if (a > hR) hR = a;
     }
-  int L = (1 + hR) / 2 + 1;
+  /* a trial reads 1 + h_R half units beyond its cell (EPI: the partner's    */
+  /* neighbours), 1 + 2 h_R under the local model (their neighbours too)     */
+  int L = local ? (1 + 2 * hR) / 2 + 1 : (1 + hR) / 2 + 1;
   if (d->min_cell > L) L = d->min_cell;
   if (L_override > 0) L = L_override;
   lay->L = L;
@@ -468,7 +471,7 @@ int orc_layout(const orc_desc *d, int32_t *L, int32_t *m) {
   shells_t sh;
   build_shells(d->kind, d->M, &sh);
   layout_t lay;
-  compute_layout(d, &sh, 0, &lay);
+  compute_layout(d, &sh, 0, &lay, 0);
   *L = lay.L;
   for (int c = 0; c < 3; ++c) m[c] = lay.m[c];
   return ORC_OK;
@@ -495,6 +498,8 @@ typedef struct {
   const orc_desc *d;
   const shells_t *sh;
   const int64_t *V;
+  const int64_t *T; /* local-energy table (non-NULL: local model, V unused) */
+  int zt;           /* its count axis length */
   uint8_t *occ;
   uint32_t t;
   int shift[3];
@@ -502,6 +507,9 @@ typedef struct {
   const uint32_t *tab;
   layout_t lay;
 } sweep_ctx;
+
+static int64_t local_delta_e(const orc_desc *d, const shells_t *sh, const int64_t *T, int zt,
+                             uint8_t *occ, int64_t i, int64_t j);
 
 /* All trials of one link cell (Sec. 2.2), in raster order: basis fastest,  */
 /* then shifted x, y, z.  Trial k of cell cid in sweep t draws              */
@@ -537,7 +545,8 @@ static void run_cell(sweep_ctx *cx, uint32_t cid, orc_stats *st) {
           st->attempts++;
           if (cx->occ[i] == cx->occ[j]) continue;
           st->unlike++;
-          int64_t dE = delta_e(d, cx->sh, cx->V, cx->occ, i, j);
+          int64_t dE = cx->T ? local_delta_e(d, cx->sh, cx->T, cx->zt, cx->occ, i, j)
+                             : delta_e(d, cx->sh, cx->V, cx->occ, i, j);
           if (accept_move(dE, wb, cx->mode, cx->s, cx->tab)) {
             uint8_t tmp = cx->occ[i];
             cx->occ[i] = cx->occ[j];
@@ -574,8 +583,9 @@ static int validate_occ(const orc_desc *d, const uint8_t *occ) {
 /* n_sweeps full MC steps starting at sweep counter t0; temperature linear    */
 /* from T_first to T_last over the call.  per_sweep[s] receives the integer   */
 /* statistics of sweep s.                                                      */
-int orc_sweeps(const orc_desc *d, const int64_t *V, uint8_t *occ, uint32_t t0, uint32_t n_sweeps,
-               double T_first, double T_last, orc_stats *per_sweep, const orc_opts *opts) {
+static int sweeps_impl(const orc_desc *d, const int64_t *V, const int64_t *T, int zt, uint8_t *occ,
+                       uint32_t t0, uint32_t n_sweeps, double T_first, double T_last,
+                       orc_stats *per_sweep, const orc_opts *opts) {
   if (!valid_desc(d) || !validate_occ(d, occ)) return ORC_EINVAL;
   shells_t sh;
   build_shells(d->kind, d->M, &sh);
@@ -583,8 +593,10 @@ int orc_sweeps(const orc_desc *d, const int64_t *V, uint8_t *occ, uint32_t t0, u
   cx.d = d;
   cx.sh = &sh;
   cx.V = V;
+  cx.T = T;
+  cx.zt = zt;
   cx.occ = occ;
-  compute_layout(d, &sh, opts ? opts->L_override : 0, &cx.lay);
+  compute_layout(d, &sh, opts ? opts->L_override : 0, &cx.lay, T != NULL);
   uint32_t n_cells = (uint32_t)cx.lay.m[0] * cx.lay.m[1] * cx.lay.m[2];
   uint32_t *order = (uint32_t *)malloc(sizeof(uint32_t) * n_cells);
   if (!order) return ORC_EINVAL;
@@ -624,6 +636,11 @@ int orc_sweeps(const orc_desc *d, const int64_t *V, uint8_t *occ, uint32_t t0, u
   return ORC_OK;
 }
 
+int orc_sweeps(const orc_desc *d, const int64_t *V, uint8_t *occ, uint32_t t0, uint32_t n_sweeps,
+               double T_first, double T_last, orc_stats *per_sweep, const orc_opts *opts) {
+  return sweeps_impl(d, V, NULL, 0, occ, t0, n_sweeps, T_first, T_last, per_sweep, opts);
+}
+
 /* The trials of a chosen set of cells of one colour phase of sweep t (cells */
 /* of one colour never interact, so any subset can be replayed alone).  Used */
 /* to check sampled cells of lattices too large for full oracle sweeps.      */
@@ -636,8 +653,10 @@ int orc_phase_cells(const orc_desc *d, const int64_t *V, uint8_t *occ, uint32_t 
   cx.d = d;
   cx.sh = &sh;
   cx.V = V;
+  cx.T = NULL;
+  cx.zt = 0;
   cx.occ = occ;
-  compute_layout(d, &sh, 0, &cx.lay);
+  compute_layout(d, &sh, 0, &cx.lay, 0);
   uint32_t tab[3 * 512];
   int code = orc_thresholds(T, tab, &cx.s, &cx.mode);
   if (code != ORC_OK) return code;
@@ -808,4 +827,131 @@ int orc_clusters(const orc_desc *d, const uint8_t *occ, uint32_t mask, uint64_t 
   free(par);
   free(cnt);
   return ORC_OK;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Local-energy model.  The paper's second model (qSRO, Sec. 3) is a general */
+/* nonlinear short-range model: a trial's energy change comes from the local */
+/* energies of all the sites of its interaction zone, each recomputed.  Its  */
+/* functional form is not printed; the reading taken here:                    */
+/*   E = sum_i eps(i),   eps(i) = sum_m sum_s T_m[s_i][s][c_{i,m,s}],         */
+/* c_{i,m,s} = the number of shell-m displacements of i that land on species */
+/* s (each displacement counted, so a site reached twice on a tiny periodic  */
+/* lattice counts twice).  T: [M][K][K][zt] int64 in q units, zt = 1 + the   */
+/* largest z_m in use; any function of each count (EPI is the linear case    */
+/* T_m[a][s][c] = c V_m(a, s) / 2).  A swap of i and j changes eps only on   */
+/* U = {i, j} u shells(i) u shells(j) (shells are closed under negation), so */
+/* dE = sum over the distinct sites k of U of eps_after(k) - eps_before(k).  */
+/* The trial reads up to 1 + 2 h_R half units from its cell, hence the link  */
+/* cells of edge floor((1 + 2 h_R)/2) + 1.  M <= 3, K <= 8.                   */
+/* ------------------------------------------------------------------------ */
+#define ORC_LOCAL_MAX_K 8
+#define ORC_LOCAL_MAX_M 3
+
+static int local_width(const shells_t *sh) {
+  int z = 0;
+  for (int m = 0; m < sh->M; ++m)
+    if (sh->z[m] > z) z = sh->z[m];
+  return z + 1;
+}
+
+int orc_local_width(int kind, int M) {
+  shells_t sh;
+  if ((kind != 0 && kind != 1) || M < 1 || M > ORC_LOCAL_MAX_M) return -1;
+  if (build_shells(kind, M, &sh) != ORC_OK) return -1;
+  return local_width(&sh);
+}
+
+static int valid_local(const orc_desc *d) {
+  return valid_desc(d) && d->M <= ORC_LOCAL_MAX_M && d->K <= ORC_LOCAL_MAX_K;
+}
+
+/* eps of site k: its species and the species counts of each of its shells */
+static int64_t local_eps(const orc_desc *d, const shells_t *sh, const int64_t *T, int zt,
+                         const uint8_t *occ, int64_t k) {
+  const int K = d->K;
+  int64_t e = 0;
+  for (int m = 0; m < sh->M; ++m) {
+    int cnt[ORC_LOCAL_MAX_K] = {0};
+    for (int t = sh->start[m]; t < sh->start[m + 1]; ++t) cnt[occ[neighbour(d, k, sh->disp[t])]]++;
+    for (int s = 0; s < K; ++s) e += T[(((int64_t)m * K + occ[k]) * K + s) * zt + cnt[s]];
+  }
+  return e;
+}
+
+/* dE of swapping i and j: the distinct sites of U, each eps evaluated with  */
+/* the occupancy before and after the swap (the swap is undone on return).   */
+static int64_t local_delta_e(const orc_desc *d, const shells_t *sh, const int64_t *T, int zt,
+                             uint8_t *occ, int64_t i, int64_t j) {
+  int64_t U[2 + 2 * ORC_MAX_DISP];
+  int nu = 0;
+  int64_t cand[2 + 2 * ORC_MAX_DISP];
+  int nc = 0;
+  cand[nc++] = i;
+  cand[nc++] = j;
+  for (int t = 0; t < sh->total; ++t) cand[nc++] = neighbour(d, i, sh->disp[t]);
+  for (int t = 0; t < sh->total; ++t) cand[nc++] = neighbour(d, j, sh->disp[t]);
+  for (int a = 0; a < nc; ++a) {
+    int seen = 0;
+    for (int b = 0; b < nu; ++b) seen |= U[b] == cand[a];
+    if (!seen) U[nu++] = cand[a];
+  }
+  int64_t before = 0, after = 0;
+  for (int a = 0; a < nu; ++a) before += local_eps(d, sh, T, zt, occ, U[a]);
+  uint8_t tmp = occ[i];
+  occ[i] = occ[j];
+  occ[j] = tmp;
+  for (int a = 0; a < nu; ++a) after += local_eps(d, sh, T, zt, occ, U[a]);
+  occ[j] = occ[i];
+  occ[i] = tmp;
+  return after - before;
+}
+
+int orc_local_energy(const orc_desc *d, const int64_t *T, const uint8_t *occ, int64_t *E) {
+  if (!valid_local(d)) return ORC_EINVAL;
+  shells_t sh;
+  build_shells(d->kind, d->M, &sh);
+  const int zt = local_width(&sh);
+  __int128 acc = 0;
+  const int64_t N = site_count(d);
+  for (int64_t k = 0; k < N; ++k) acc += local_eps(d, &sh, T, zt, occ, k);
+  if (acc > (__int128)INT64_MAX || acc < (__int128)INT64_MIN) return ORC_EOVERFLOW;
+  *E = (int64_t)acc;
+  return ORC_OK;
+}
+
+int orc_local_delta_e(const orc_desc *d, const int64_t *T, const uint8_t *occ, int64_t i,
+                      int64_t j, int64_t *dE) {
+  if (!valid_local(d)) return ORC_EINVAL;
+  const int64_t N = site_count(d);
+  if (i < 0 || j < 0 || i >= N || j >= N) return ORC_EINVAL;
+  shells_t sh;
+  build_shells(d->kind, d->M, &sh);
+  uint8_t *o = (uint8_t *)malloc((size_t)N);
+  if (!o) return ORC_EINVAL;
+  memcpy(o, occ, (size_t)N);
+  *dE = local_delta_e(d, &sh, T, local_width(&sh), o, i, j);
+  free(o);
+  return ORC_OK;
+}
+
+int orc_local_layout(const orc_desc *d, int32_t *L, int32_t *m) {
+  if (!valid_local(d)) return ORC_EINVAL;
+  shells_t sh;
+  build_shells(d->kind, d->M, &sh);
+  layout_t lay;
+  compute_layout(d, &sh, 0, &lay, 1);
+  *L = lay.L;
+  for (int c = 0; c < 3; ++c) m[c] = lay.m[c];
+  return ORC_OK;
+}
+
+int orc_local_sweeps(const orc_desc *d, const int64_t *T, uint8_t *occ, uint32_t t0,
+                     uint32_t n_sweeps, double T_first, double T_last, orc_stats *per_sweep,
+                     const orc_opts *opts) {
+  if (!valid_local(d)) return ORC_EINVAL;
+  shells_t sh;
+  build_shells(d->kind, d->M, &sh);
+  return sweeps_impl(d, NULL, T, local_width(&sh), occ, t0, n_sweeps, T_first, T_last, per_sweep,
+                     opts);
 }

@@ -108,3 +108,21 @@ def binary_energies(kind, n, V, configs):
         assert exact[c] % 2 == 0
         exact[c] //= 2
     return exact
+
+
+def local_energies(kind, n, T, configs):
+    """Local-energy model E = sum_i sum_m sum_s T[m][s_i][s][c_{i,m,s}] of
+    many configurations (configs: [C, N] species ids), with the shell counts
+    c_{i,m,s} = sum_j mult_m(i, j) [s_j = s] taken from the brute-force
+    multiplicity matrices (every periodic image counted).  Exact integers."""
+    M, K = T.shape[0], T.shape[1]
+    configs = np.atleast_2d(np.asarray(configs, dtype=np.int64))
+    mult = multiplicity(kind, n, M)
+    onehot = (configs[:, :, None] == np.arange(K)[None, None, :]).astype(np.int64)  # [C, N, K]
+    out = np.zeros(len(configs), dtype=object)
+    for m in range(M):
+        cnt = np.einsum("ij,cjk->cik", mult[m], onehot)  # [C, N, K]
+        for s in range(K):
+            vals = T[m][configs, s, cnt[:, :, s]]  # [C, N]
+            out += np.array([int(v) for v in vals.astype(object).sum(1)], dtype=object)
+    return out
