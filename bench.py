@@ -51,10 +51,11 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
-    ap.add_argument("--mode", default="plain", choices=["plain", "batch", "serve", "slab"],
+    ap.add_argument("--mode", default="plain", choices=["plain", "batch", "serve", "slab", "local"],
                     help="plain: the single-lattice sweep (default); batch: 256 independent "
                          "lattices batched vs one at a time; serve: Poisson-arrival serving; "
-                         "slab: one lattice decomposed along z over the ranks")
+                         "slab: one lattice decomposed along z over the ranks; local: the "
+                         "local-energy (nonlinear short-range) model")
     ap.add_argument("--jobs", type=int, default=256)
     ap.add_argument("--chunk", type=int, default=50)
     ap.add_argument("--rate", type=float, default=5.0)
@@ -253,6 +254,56 @@ def _job_arrays(j):
     return V, occ
 
 
+def run_local(args):
+    """The local-energy model (the nonlinear short-range model of Sec. 3): the
+    workload's lattice and composition with a synthetic table (pairwise part
+    plus a term quadratic in each shell count, shells 1-3); every trial
+    recomputes the local energies of its interaction zone.  value = sites x
+    sweeps / CUDA-event time of the timed sweeps."""
+    import torch
+
+    torch.cuda.set_device(0)
+    from paper_2509_20949_gb300.lattice import Lattice
+
+    w, N, desc = workload_config(args.workload)
+    M = min(w["M"], 3)
+    T = inputs.local_energy_table(w["kind"], M, w["K"], w["sigma"], w["epi_seed"])
+    occ = inputs.initial_occupancy(w["kind"], w["n"], w["K"], w["occ_seed"], w["fractions"])
+    stream = torch.cuda.current_stream()
+    lat = Lattice(w["kind"], w["n"], w["K"], occ, seed=w["seed"], pack_bits=args.pack_bits,
+                  stream=stream)
+    lat.set_local_model(T)
+    for i in range(args.warmup):
+        lat.sweep(1, sweep_temperature(w, i), stats=False)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(0)
+    clocks.start()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for s in range(args.steps):
+        lat.sweep(1, sweep_temperature(w, args.warmup + s), stats=False)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    t_ms = ev0.elapsed_time(ev1)
+    ts = lat.sweep(1, sweep_temperature(w, args.warmup + args.steps))
+    L, m = lat.layout()
+    line = {"metric": "attempted MC swaps/sec on 1 GB300 (local-energy model)",
+            "value": N * args.steps / (t_ms / 1e3), "unit": UNIT, "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
+            "data": "synthetic", "mode": "local",
+            "config": {"workload": desc, "model": f"local energies of shells 1-{M}: "
+                       "T = c V/2 + U c^2/z per (shell, centre, neighbour species)",
+                       "link_cell_edge": L, "cells": m, "step": "1 sweep (8 colour phases)",
+                       "pack_bits": args.pack_bits},
+            "trial_stats": {"unlike_frac": ts["unlike"] / ts["attempts"],
+                            "accepted_frac": ts["accepted"] / ts["attempts"]},
+            "clocks": clk, "gpu_launches": args.steps * 8}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_slab(args):
     """One lattice swept by all ranks through the z decomposition (strong
     scaling): every rank holds the same lattice, sweeps its share of the link
@@ -409,6 +460,8 @@ def main():
         return run_serve(args)
     if args.mode == "slab":
         return run_slab(args)
+    if args.mode == "local":
+        return run_local(args)
     import torch
 
     world, rank, local = dist_setup()

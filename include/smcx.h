@@ -188,6 +188,40 @@ smcx_status smcx_set_sweep_counter(smcx_lattice* lat, uint32_t t);
    and cells per dimension m[3] (even, or 1). ESTATE: no EPI. */
 smcx_status smcx_get_layout(smcx_lattice* lat, uint32_t* L, uint32_t* m);
 
+/* ---- local-energy model (the nonlinear short-range model of Sec. 3) -------
+ *
+ * The paper's second model (qSRO) is a general nonlinear short-range model: a
+ * trial's energy change comes from recomputing the local energy of every
+ * site in its interaction zone.  The paper does not print its functional
+ * form; this library reads it as per-site energies that are tabulated
+ * functions of the site's shell-resolved species counts:
+ *   E = sum_i eps(i),  eps(i) = sum_m sum_s T_m[s_i][s][c_{i,m,s}],
+ * c_{i,m,s} = the number of shell-m neighbours of i holding species s (each
+ * shell displacement counted).  Any function of each count can be tabulated
+ * (EPI is the linear case T_m[a][s][c] = c V_m(a, s) / 2).  A swap of i and j
+ * changes eps only on U = {i, j} u shells(i) u shells(j); the kernel
+ * recomputes eps before and after the swap on every distinct site of U.  A
+ * trial then reads up to 1 + 2 h_R half units from its cell, so the link
+ * cells grow to edge floor((1 + 2 h_R)/2) + 1.  The trial schedule, random
+ * numbers and Metropolis test are those of the EPI sweep. */
+
+/* Length zt of the count axis of a local-energy table: 1 + the largest
+   coordination number of shells 1..n_shells.  0 for kind > 1 or n_shells
+   outside 1..3. */
+uint32_t smcx_local_model_width(uint32_t kind, uint32_t n_shells);
+
+/* Replaces the lattice's energy model by the local-energy model with table
+   t_q: [n_shells][K][K][zt] int64 q units (host, read during the call),
+   entry [m][a][s][c] = the energy of a site of species a whose shell m+1
+   holds c sites of species s.  Every later smcx_sweep / smcx_run_colour /
+   smcx_energy / smcx_running_energy uses it (the SRO pair counts do not
+   depend on the model); smcx_set_epi switches back.  Restarts the running
+   energy.  EINVAL: n_shells outside 1..3, K > 8, some n_d < 4, or a table
+   value beyond 2^48 in magnitude.  Checkpoints hold EPI lattices only
+   (smcx_checkpoint returns ESTATE under this model), and the z
+   decomposition plans are for EPI link cells. */
+smcx_status smcx_set_local_model(smcx_lattice* lat, uint32_t n_shells, const int64_t* t_q);
+
 /* ---- lattice decomposition along z (Sec. 2.2, lattice parallelism) -------
  *
  * The paper splits one lattice over several GPUs, each sweeping its own part

@@ -142,6 +142,8 @@ SIGNATURES = {
     "smcx_slab_transfer": (_st, [_P(LatticeDesc), ctypes.c_uint32, ctypes.c_uint32,
                                  ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32,
                                  _P(ctypes.c_int32), _P(ctypes.c_uint32)]),
+    "smcx_local_model_width": (ctypes.c_uint32, [ctypes.c_uint32, ctypes.c_uint32]),
+    "smcx_set_local_model": (_st, [_vp, ctypes.c_uint32, _vp]),
     "smcx_planes_bytes": (ctypes.c_size_t, [_vp, ctypes.c_uint32]),
     "smcx_get_planes": (_st, [_vp, ctypes.c_int32, ctypes.c_uint32, _vp]),
     "smcx_put_planes": (_st, [_vp, ctypes.c_int32, ctypes.c_uint32, _vp]),

@@ -109,4 +109,14 @@ cudaError_t launch_clusters(const Geom& g, const uint8_t* occ, uint32_t mask, ui
 cudaError_t launch_merge_planes(uint8_t* occ, const uint8_t* theirs, const uint8_t* before,
                                 size_t bytes, int n_sm, cudaStream_t st);
 
+// local-energy model: one colour phase over cells z index az0 .. az0 + naz
+// (a.naz > 0), and the total energy as n_blocks int64 partial sums.  lp and T
+// are device copies (T: [M][K][K][zt] int64, n_T entries).
+cudaError_t launch_sweep_local(const Geom& g, const PhaseArgs& a, const Tables& tab,
+                               uint8_t* occ, const LocalParam* lp, const int64_t* T, int n_T,
+                               unsigned long long* stats, cudaStream_t st);
+cudaError_t launch_local_energy(const Geom& g, const LocalParam* lp, const int64_t* T, int n_T,
+                                const uint8_t* occ, long long* partial, int n_blocks,
+                                cudaStream_t st);
+
 }  // namespace smcx

@@ -379,4 +379,266 @@ cudaError_t launch_philox_fill(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c
   return cudaGetLastError();
 }
 
+// ---- local-energy model (the nonlinear short-range model of Sec. 3) ------
+//
+// One thread per active link cell, trials in the raster order and Philox
+// keying of the EPI kernels.  A trial's energy change is the sum over the
+// distinct sites k of U (LocalParam::u, displacements from i) of eps_after(k)
+// - eps_before(k).  For k = i and k = j every shell is recounted before and
+// after the swap (5-bit one-hot fields of a 64-bit word; the swapped sites are
+// recognised by their site ids).  Any other k keeps its species, and its
+// shell m+1 changes only when exactly one of i, j lies in it (i turns p -> q,
+// j turns q -> p; both together cancel): only those shells are scanned, for
+// the counts of p and q, and four table entries change.  Integer throughout.
+
+__device__ __forceinline__ uint32_t count_field(uint64_t c, int s) {
+  return static_cast<uint32_t>((c >> (5 * s)) & 31u);
+}
+
+// neighbour for displacements shorter than the period (|d| < 2 n_d half
+// units): one conditional wrap per axis instead of a modulo
+__device__ __forceinline__ SiteXYZ neighbour_near(const Geom& g, const SiteXYZ& s, int dx, int dy,
+                                                  int dz) {
+  int hx = 2 * s.x + basis_comp(g.kind, s.b, 0) + dx;
+  int hy = 2 * s.y + basis_comp(g.kind, s.b, 1) + dy;
+  int hz = 2 * s.z + basis_comp(g.kind, s.b, 2) + dz;
+  hx += hx < 0 ? 2 * g.n[0] : (hx >= 2 * g.n[0] ? -2 * g.n[0] : 0);
+  hy += hy < 0 ? 2 * g.n[1] : (hy >= 2 * g.n[1] ? -2 * g.n[1] : 0);
+  hz += hz < 0 ? 2 * g.n[2] : (hz >= 2 * g.n[2] ? -2 * g.n[2] : 0);
+  SiteXYZ r;
+  r.x = hx >> 1;
+  r.y = hy >> 1;
+  r.z = hz >> 1;
+  r.b = basis_of_parity(g.kind, hx & 1, hy & 1, hz & 1);
+  return r;
+}
+
+// eps_after(k) - eps_before(k) for k = i or j (species cb before, ca after)
+__device__ __forceinline__ int64_t local_eps_change(const Geom& g, const LocalParam& lp,
+                                                    const int64_t* T, const uint8_t* occ,
+                                                    const SiteXYZ& sk, uint32_t cb, uint32_t ca,
+                                                    uint32_t ii, uint32_t jj, uint32_t p,
+                                                    uint32_t q) {
+  int64_t de = 0;
+  const int K = lp.K, zt = lp.zt;
+  for (int m = 0; m < lp.M; ++m) {
+    uint64_t nb_b = 0, nb_a = 0;
+    for (int t = lp.start[m]; t < lp.start[m + 1]; ++t) {
+      const SiteXYZ sn = neighbour_near(g, sk, lp.v[t][0], lp.v[t][1], lp.v[t][2]);
+      const uint32_t nn = site_id(g, sn);
+      const uint32_t sb = occ_get(g, occ, sn);
+      const uint32_t sa = nn == ii ? q : (nn == jj ? p : sb);
+      nb_b += 1ull << (5 * sb);
+      nb_a += 1ull << (5 * sa);
+    }
+    const int64_t* row_b = T + (static_cast<size_t>(m) * K + cb) * K * zt;
+    const int64_t* row_a = T + (static_cast<size_t>(m) * K + ca) * K * zt;
+    for (int s = 0; s < K; ++s)
+      de += row_a[s * zt + count_field(nb_a, s)] - row_b[s * zt + count_field(nb_b, s)];
+  }
+  return de;
+}
+
+// eps change of a site k other than i and j (species c): in each shell m+1
+// holding exactly one of them, the counts of p and q move by one
+__device__ __forceinline__ int64_t local_bystander_change(const Geom& g, const LocalParam& lp,
+                                                          const int64_t* T, const uint8_t* occ,
+                                                          const SiteXYZ& sk, uint32_t c,
+                                                          uint32_t shells_i, uint32_t shells_j,
+                                                          uint32_t p, uint32_t q) {
+  int64_t de = 0;
+  const int K = lp.K, zt = lp.zt;
+  const uint32_t one = shells_i ^ shells_j;
+  for (int m = 0; m < lp.M; ++m) {
+    if (!((one >> m) & 1u)) continue;
+    int np = 0, nq = 0;
+    for (int t = lp.start[m]; t < lp.start[m + 1]; ++t) {
+      const uint32_t sn = occ_get(g, occ, neighbour_near(g, sk, lp.v[t][0], lp.v[t][1], lp.v[t][2]));
+      np += sn == p;
+      nq += sn == q;
+    }
+    const int dp = ((shells_i >> m) & 1u) ? -1 : 1;  // i: p -> q; j: q -> p
+    const int64_t* row = T + (static_cast<size_t>(m) * K + c) * K * zt;
+    de += row[p * zt + np + dp] - row[p * zt + np] + row[q * zt + nq - dp] - row[q * zt + nq];
+  }
+  return de;
+}
+
+constexpr int kLocalParamBytes = (sizeof(LocalParam) + 15) / 16 * 16;
+
+__device__ void load_local(unsigned char* smem, const LocalParam* lp_g, const int64_t* T_g,
+                           int n_T) {
+  const uint32_t* src = reinterpret_cast<const uint32_t*>(lp_g);
+  uint32_t* dst = reinterpret_cast<uint32_t*>(smem);
+  for (int w = threadIdx.x; w < static_cast<int>(sizeof(LocalParam) / 4); w += blockDim.x)
+    dst[w] = src[w];
+  int64_t* t = reinterpret_cast<int64_t*>(smem + kLocalParamBytes);
+  for (int w = threadIdx.x; w < n_T; w += blockDim.x) t[w] = T_g[w];
+}
+
+__global__ void __launch_bounds__(128) k_sweep_local(const __grid_constant__ Geom g,
+                                                    const PhaseArgs a,
+                                                    const __grid_constant__ Tables tab,
+                                                    uint8_t* __restrict__ occ,
+                                                    const LocalParam* __restrict__ lp_g,
+                                                    const int64_t* __restrict__ T_g, int n_T,
+                                                    unsigned long long* __restrict__ stats,
+                                                    uint32_t n_active, uint32_t ax_n,
+                                                    uint32_t ay_n) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  load_local(smem, lp_g, T_g, n_T);
+  uint32_t* s_tab = reinterpret_cast<uint32_t*>(smem + kLocalParamBytes + 8 * n_T);
+  for (int w = threadIdx.x; w < kTabWords; w += blockDim.x) s_tab[w] = tab.w[w];
+  __syncthreads();
+  const LocalParam& lp = *reinterpret_cast<const LocalParam*>(smem);
+  const int64_t* T = reinterpret_cast<const int64_t*>(smem + kLocalParamBytes);
+
+  uint64_t att = 0, unl = 0, acc = 0;
+  int64_t sum_de = 0;
+  const uint32_t tid = blockIdx.x * blockDim.x + threadIdx.x;
+  if (tid < n_active) {
+    const uint32_t axi = tid % ax_n, ayi = (tid / ax_n) % ay_n,
+                   azi = tid / (ax_n * ay_n) + static_cast<uint32_t>(a.az0);
+    const int c[3] = {
+        g.m[0] == 1 ? 0 : static_cast<int>(2 * axi + (a.colour & 1)),
+        g.m[1] == 1 ? 0 : static_cast<int>(2 * ayi + ((a.colour >> 1) & 1)),
+        g.m[2] == 1 ? 0 : static_cast<int>(2 * azi + ((a.colour >> 2) & 1))};
+    const uint32_t cid = (static_cast<uint32_t>(c[2]) * g.m[1] + c[1]) * g.m[0] + c[0];
+    int lo[3], hi[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      lo[d] = static_cast<int>((static_cast<int64_t>(c[d]) * g.n[d]) / g.m[d]);
+      hi[d] = static_cast<int>((static_cast<int64_t>(c[d] + 1) * g.n[d]) / g.m[d]);
+    }
+    uint32_t k = 0;
+    U4 w = {0, 0, 0, 0};
+    for (int zs = lo[2]; zs < hi[2]; ++zs)
+      for (int ys = lo[1]; ys < hi[1]; ++ys)
+        for (int xs = lo[0]; xs < hi[0]; ++xs)
+          for (int b = 0; b < g.nb; ++b, ++k) {
+            SiteXYZ si;
+            si.x = pmod(xs + a.shift[0], g.n[0]);
+            si.y = pmod(ys + a.shift[1], g.n[1]);
+            si.z = pmod(zs + a.shift[2], g.n[2]);
+            si.b = b;
+            if ((k & 1u) == 0) w = philox4x32_10(k >> 1, cid, a.t, 0u, g.seed_lo, g.seed_hi);
+            const uint32_t wa = (k & 1u) ? w.z : w.x;
+            const uint32_t wb = (k & 1u) ? w.w : w.y;
+            const uint32_t dir = __umulhi(wa, static_cast<uint32_t>(g.z1));
+            const SiteXYZ sj = neighbour_near(g, si, lp.v[dir][0], lp.v[dir][1], lp.v[dir][2]);
+            const uint32_t p = occ_get(g, occ, si), q = occ_get(g, occ, sj);
+            ++att;
+            if (p == q) continue;
+            ++unl;
+            const uint32_t ii = site_id(g, si), jj = site_id(g, sj);
+            int64_t de = 0;
+            de += local_eps_change(g, lp, T, occ, si, p, q, ii, jj, p, q) +
+                  local_eps_change(g, lp, T, occ, sj, q, p, ii, jj, p, q);
+            for (int e = 2; e < lp.n_u[dir]; ++e) {
+              const uint32_t mi = lp.shells_i[dir][e], mj = lp.shells_j[dir][e];
+              if (mi == mj) continue;  // no shell holds exactly one of i, j
+              const SiteXYZ sk =
+                  neighbour_near(g, si, lp.u[dir][e][0], lp.u[dir][e][1], lp.u[dir][e][2]);
+              de += local_bystander_change(g, lp, T, occ, sk, occ_get(g, occ, sk), mi, mj, p, q);
+            }
+            bool accept;
+            if (de <= 0 || a.mode == kModeAcceptAll) {
+              accept = true;
+            } else if (a.mode == kModeZeroT) {
+              accept = false;
+            } else {
+              const uint64_t idx = static_cast<uint64_t>(de) >> a.s;
+              accept = idx < (1ull << 27) &&
+                       wb < compose_threshold(s_tab[idx & 511u], s_tab[512 + ((idx >> 9) & 511u)],
+                                              s_tab[1024 + (idx >> 18)]);
+            }
+            if (accept) {
+              occ_set(g, occ, si, q);
+              occ_set(g, occ, sj, p);
+              ++acc;
+              sum_de += de;
+            }
+          }
+  }
+  warp_reduce_add_stats(stats, att, unl, acc, sum_de);
+}
+
+// Total local energy: per-block int64 partial sums (the host adds them in
+// int128); one thread per conventional cell, grid-stride
+__global__ void __launch_bounds__(256) k_local_energy(const Geom g,
+                                                      const LocalParam* __restrict__ lp_g,
+                                                      const int64_t* __restrict__ T_g, int n_T,
+                                                      const uint8_t* __restrict__ occ,
+                                                      long long* __restrict__ partial,
+                                                      uint32_t n_cells) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ long long s_red[8];
+  load_local(smem, lp_g, T_g, n_T);
+  __syncthreads();
+  const LocalParam& lp = *reinterpret_cast<const LocalParam*>(smem);
+  const int64_t* T = reinterpret_cast<const int64_t*>(smem + kLocalParamBytes);
+  const int K = lp.K, zt = lp.zt;
+  long long e = 0;
+  for (uint32_t cell = blockIdx.x * blockDim.x + threadIdx.x; cell < n_cells;
+       cell += gridDim.x * blockDim.x) {
+    SiteXYZ s;
+    s.x = static_cast<int>(cell % g.n[0]);
+    s.y = static_cast<int>((cell / g.n[0]) % g.n[1]);
+    s.z = static_cast<int>(cell / (static_cast<uint32_t>(g.n[0]) * g.n[1]));
+    for (int b = 0; b < g.nb; ++b) {
+      s.b = b;
+      const uint32_t c = occ_get(g, occ, s);
+      for (int m = 0; m < lp.M; ++m) {
+        uint64_t nb = 0;
+        for (int t = lp.start[m]; t < lp.start[m + 1]; ++t)
+          nb += 1ull << (5 * occ_get(g, occ, neighbour(g, s, lp.v[t][0], lp.v[t][1], lp.v[t][2])));
+        const int64_t* row = T + (static_cast<size_t>(m) * K + c) * K * zt;
+        for (int sp = 0; sp < K; ++sp) e += row[sp * zt + count_field(nb, sp)];
+      }
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) e += __shfl_down_sync(0xffffffffu, e, o);
+  if ((threadIdx.x & 31) == 0) s_red[threadIdx.x >> 5] = e;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    long long t = 0;
+    for (int w = 0; w < static_cast<int>(blockDim.x >> 5); ++w) t += s_red[w];
+    partial[blockIdx.x] = t;
+  }
+}
+
+size_t local_smem_bytes(int n_T) { return kLocalParamBytes + 8 * static_cast<size_t>(n_T); }
+
+cudaError_t launch_sweep_local(const Geom& g, const PhaseArgs& a, const Tables& tab,
+                               uint8_t* occ, const LocalParam* lp, const int64_t* T, int n_T,
+                               unsigned long long* stats, cudaStream_t st) {
+  uint32_t cnt[2];
+  for (int d = 0; d < 2; ++d) {
+    if (g.m[d] == 1 && ((a.colour >> d) & 1)) return cudaSuccess;
+    cnt[d] = g.m[d] == 1 ? 1u : static_cast<uint32_t>(g.m[d] / 2);
+  }
+  if (a.naz <= 0) return cudaErrorInvalidValue;
+  const uint32_t n_active = cnt[0] * cnt[1] * static_cast<uint32_t>(a.naz);
+  const size_t smem = local_smem_bytes(n_T) + 4 * kTabWords;
+  cudaError_t e = cudaFuncSetAttribute(k_sweep_local, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       static_cast<int>(smem));
+  if (e != cudaSuccess) return e;
+  k_sweep_local<<<(n_active + 127) / 128, 128, smem, st>>>(g, a, tab, occ, lp, T, n_T, stats,
+                                                          n_active, cnt[0], cnt[1]);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_local_energy(const Geom& g, const LocalParam* lp, const int64_t* T, int n_T,
+                                const uint8_t* occ, long long* partial, int n_blocks,
+                                cudaStream_t st) {
+  const size_t smem = local_smem_bytes(n_T);
+  cudaError_t e = cudaFuncSetAttribute(k_local_energy, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       static_cast<int>(smem));
+  if (e != cudaSuccess) return e;
+  const uint32_t n_cells = static_cast<uint32_t>(g.n[0]) * g.n[1] * g.n[2];
+  k_local_energy<<<n_blocks, 256, smem, st>>>(g, lp, T, n_T, occ, partial, n_cells);
+  return cudaGetLastError();
+}
+
 }  // namespace smcx

@@ -2,6 +2,7 @@
 // link-cell layout, the per-sweep schedule (origin shift, colours, Metropolis
 // threshold tables) and kernel launches.  Host code only; the kernels live in
 // kernels_*.cu.
+#include <array>
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
@@ -90,9 +91,24 @@ struct WorkLayout {
   size_t V;        // [4][K][K] int64
   size_t D;        // per-(p, q) difference rows of the tiled kernel
   size_t pairs;    // [4][K][K] u64
+  size_t local;    // K <= 8: LocalParam, the local-energy table, energy partial sums
   size_t scratch;  // N bytes: canonical occupancy in transit
   size_t total;
 };
+
+constexpr int kLocalPartials = 2048;  // blocks of the local-energy reduction
+constexpr size_t kLocalParamOff = 0;
+constexpr size_t kLocalTableOff = (sizeof(LocalParam) + 255) / 256 * 256;
+
+size_t local_table_bytes(size_t K) {
+  return sizeof(int64_t) * kLocalMaxShells * K * K * kLocalMaxZT;
+}
+
+size_t local_bytes(size_t K) {
+  if (K > static_cast<size_t>(kLocalMaxK)) return 0;
+  return kLocalTableOff + align_up(local_table_bytes(K), 256) +
+         align_up(sizeof(long long) * kLocalPartials, 256);
+}
 
 constexpr size_t kTiledTableWords = 6 * 6 * 160 / 4;  // largest table: K = 6, M = 4
 
@@ -104,7 +120,8 @@ WorkLayout work_layout(const smcx_lattice_desc* d) {
   w.D = w.V + align_up(sizeof(int64_t) * kMaxShells * K * K, 256);
   w.pairs = w.D + align_up(sizeof(uint32_t) * kTiledTableWords, 256);
   const size_t kp = K < 6 ? 6 : K;  // the tiled pair count writes [4][6][6] at most
-  w.scratch = w.pairs + align_up(sizeof(uint64_t) * kMaxShells * kp * kp, 256);
+  w.local = w.pairs + align_up(sizeof(uint64_t) * kMaxShells * kp * kp, 256);
+  w.scratch = w.local + local_bytes(K);
   w.total = w.scratch + align_up(static_cast<size_t>(n_sites(d)), 256);
   return w;
 }
@@ -194,6 +211,9 @@ struct smcx_lattice {
   int opt_tile = -1;
   int n_sm = 0;
   bool tiled_table_ok = false;  // the tiled kernel's int32 difference table fits
+  bool local = false;           // the local-energy model replaces the EPI model
+  int zt = 0;                   // its table's count axis
+  int n_T = 0;                  // its table's entries
   int tiled_kmax = 0;
   // online kernel choice (SMCX_OPT_KERNEL = 0 and SMCX_OPT_TILE = -1): the
   // candidates (kernel, tile shape), the fastest phase seen for each, and
@@ -220,6 +240,12 @@ struct smcx_lattice {
   uint8_t* scratch() { return d_work + wl.scratch; }
   uint32_t* dtab() { return reinterpret_cast<uint32_t*>(d_work + wl.D); }
   unsigned int* flag() { return reinterpret_cast<unsigned int*>(stats() + kStatStatus); }
+  LocalParam* dlp() { return reinterpret_cast<LocalParam*>(d_work + wl.local + kLocalParamOff); }
+  int64_t* dT() { return reinterpret_cast<int64_t*>(d_work + wl.local + kLocalTableOff); }
+  long long* dpart() {
+    return reinterpret_cast<long long*>(d_work + wl.local + kLocalTableOff +
+                                        align_up(local_table_bytes(desc.n_species), 256));
+  }
   Geom geom() const;
 };
 
@@ -262,9 +288,11 @@ Geom geom_of(const smcx_lattice_desc& desc, int M, int L, const int m[3]) {
 // link cells: edge L = floor((1 + h_R)/2) + 1 (two same-colour cells then never
 // share a site one writes and the other reads), raised to min_cell; per
 // dimension the largest even count <= n/L, or 1.
-void layout_of(const smcx_lattice_desc& d, int M, int* L_out, int m[3]) {
+void layout_of(const smcx_lattice_desc& d, int M, int* L_out, int m[3], bool local = false) {
   const int hR = shell_reach(static_cast<int>(d.kind), M);
-  int L = (1 + hR) / 2 + 1;
+  // a trial reads 1 + h_R half units beyond its cell (the partner's
+  // neighbours), 1 + 2 h_R under the local-energy model (theirs too)
+  int L = local ? (1 + 2 * hR) / 2 + 1 : (1 + hR) / 2 + 1;
   if (static_cast<int>(d.min_cell) > L) L = static_cast<int>(d.min_cell);
   *L_out = L;
   for (int c = 0; c < 3; ++c) {
@@ -313,7 +341,9 @@ ShellParam shell_param(int kind) {
   return sp;
 }
 
-void compute_layout(smcx_lattice* lat) { layout_of(lat->desc, static_cast<int>(lat->M), &lat->L, lat->m); }
+void compute_layout(smcx_lattice* lat) {
+  layout_of(lat->desc, static_cast<int>(lat->M), &lat->L, lat->m, lat->local);
+}
 
 smcx_status validate_occupancy(const smcx_lattice_desc& d, const uint8_t* h) {
   const uint64_t N = n_sites(&d);
@@ -407,7 +437,26 @@ smcx_status energy_from_counts(smcx_lattice* lat, const std::vector<uint64_t>& c
   return SMCX_OK;
 }
 
+// Local-energy model: per-block int64 partial sums of the site energies,
+// added on the host in int128.
+smcx_status local_energy(smcx_lattice* lat, int64_t* e) {
+  const Geom g = lat->geom();
+  SMCX_CUDA(lat, launch_local_energy(g, lat->dlp(), lat->dT(), lat->n_T, lat->d_occ, lat->dpart(),
+                                     kLocalPartials, lat->stream));
+  std::vector<long long> part(kLocalPartials);
+  SMCX_CUDA(lat, cudaMemcpyAsync(part.data(), lat->dpart(), sizeof(long long) * kLocalPartials,
+                                 cudaMemcpyDeviceToHost, lat->stream));
+  SMCX_CUDA(lat, cudaStreamSynchronize(lat->stream));
+  __int128 acc = 0;
+  for (long long v : part) acc += v;
+  if (acc > static_cast<__int128>(INT64_MAX) || acc < static_cast<__int128>(INT64_MIN))
+    return fail(SMCX_EOVERFLOW, "energy does not fit int64");
+  *e = static_cast<int64_t>(acc);
+  return SMCX_OK;
+}
+
 smcx_status full_energy(smcx_lattice* lat, int64_t* e) {
+  if (lat->local) return local_energy(lat, e);
   std::vector<uint64_t> cnt;
   smcx_status s = run_pair_counts(lat, lat->M, &cnt);
   if (s != SMCX_OK) return s;
@@ -442,6 +491,7 @@ bool cell_ok(smcx_lattice* lat) { return lat->tiled_table_ok && cell_supported(l
 // the requested kernel cannot run the lattice).  Automatic: the tuned
 // choice, and before tuning has finished tiled, else cell, else generic.
 int kernel_choice(smcx_lattice* lat) {
+  if (lat->local) return 4;  // the local-energy model has one kernel
   switch (lat->opt_kernel) {
     case 1: return 1;
     case 2: return tiled_shape_for(lat) >= 0 ? 2 : 0;
@@ -460,7 +510,7 @@ void tuning_reset(smcx_lattice* lat) {
   tu.cands.clear();
   tu.next = 0;
   tu.choice = 0;
-  if (lat->has_epi && lat->tiled_table_ok) {
+  if (lat->has_epi && lat->tiled_table_ok && !lat->local) {
     const Geom g = lat->geom();
     for (int sh = 0; sh < tiled_shape_count(g.kind); ++sh)
       if (tiled_supported(g, sh)) tu.cands.emplace_back(2, sh);
@@ -510,6 +560,11 @@ smcx_status launch_colour_with(smcx_lattice* lat, int colour, const PhaseArgs& b
   if (a.naz == 0) return SMCX_OK;  // no cell of this colour in the range
   if (kern == 0)
     return fail(SMCX_EINVAL, "the requested kernel does not support this lattice/EPI/tile shape");
+  if (kern == 4) {
+    SMCX_CUDA(lat, launch_sweep_local(g, a, tab, lat->d_occ, lat->dlp(), lat->dT(), lat->n_T,
+                                      lat->stats(), lat->stream));
+    return SMCX_OK;
+  }
   if (kern == 3) {
     SMCX_CUDA(lat, launch_sweep_cells(g, a, tab, lat->d_occ,
                                       reinterpret_cast<const uint8_t*>(lat->dtab()), lat->stats(),
@@ -690,6 +745,7 @@ smcx_status smcx_set_epi(smcx_lattice* lat, uint32_t n_shells, const int64_t* v_
         if (v >= vmax || v <= -vmax) return fail(SMCX_EINVAL, "EPI value beyond 2^52 q");
       }
   lat->M = n_shells;
+  lat->local = false;
   lat->V.assign(v_q, v_q + n_shells * K * K);
   compute_layout(lat);
   std::vector<int64_t> vpad(kMaxShells * K * K, 0);
@@ -707,6 +763,93 @@ smcx_status smcx_set_epi(smcx_lattice* lat, uint32_t n_shells, const int64_t* v_
   s = restart_running_energy(lat);
   if (s != SMCX_OK) lat->has_epi = false;
   return s;
+}
+
+uint32_t smcx_local_model_width(uint32_t kind, uint32_t n_shells) {
+  if (kind > 1 || n_shells < 1 || n_shells > static_cast<uint32_t>(kLocalMaxShells)) return 0;
+  int z = 0;
+  for (uint32_t m = 0; m < n_shells; ++m) z = std::max(z, shell_z(static_cast<int>(kind), m));
+  return static_cast<uint32_t>(z + 1);
+}
+
+smcx_status smcx_set_local_model(smcx_lattice* lat, uint32_t n_shells, const int64_t* t_q) {
+  smcx_status s = check_handle(lat);
+  if (s != SMCX_OK) return s;
+  const int kind = static_cast<int>(lat->desc.kind);
+  const uint32_t zt = smcx_local_model_width(lat->desc.kind, n_shells);
+  if (zt == 0) return fail(SMCX_EINVAL, "n_shells must be 1..3 for the local-energy model");
+  const size_t K = lat->desc.n_species;
+  if (K > static_cast<size_t>(kLocalMaxK)) return fail(SMCX_EINVAL, "local-energy model: K <= 8");
+  if (!t_q) return fail(SMCX_EINVAL, "null table");
+  for (int d = 0; d < 3; ++d)
+    if (lat->desc.n[d] < 4) return fail(SMCX_EINVAL, "local-energy model: every n_d >= 4");
+  const size_t n_T = static_cast<size_t>(n_shells) * K * K * zt;
+  for (size_t i = 0; i < n_T; ++i)
+    if (t_q[i] > kLocalMaxAbsT || t_q[i] < -kLocalMaxAbsT)
+      return fail(SMCX_EINVAL, "local-energy table value beyond 2^48 q");
+  LocalParam lp;
+  std::memset(&lp, 0, sizeof(lp));
+  lp.M = static_cast<int>(n_shells);
+  lp.K = static_cast<int>(K);
+  lp.zt = static_cast<int>(zt);
+  lp.total = shell_start(kind, lp.M);
+  for (int m = 0; m <= lp.M; ++m) lp.start[m] = shell_start(kind, m);
+  for (int t = 0; t < lp.total; ++t) {
+    const ShellVec v = shell_vec(kind, t);
+    lp.v[t][0] = static_cast<int8_t>(v.x);
+    lp.v[t][1] = static_cast<int8_t>(v.y);
+    lp.v[t][2] = static_cast<int8_t>(v.z);
+  }
+  // U as distinct displacements from i: 0, the partner d, the shell vectors,
+  // and d plus each shell vector
+  const int z1 = shell_z(kind, 0);
+  for (int dir = 0; dir < z1; ++dir) {
+    const ShellVec d = shell_vec(kind, dir);
+    std::vector<std::array<int, 3>> u;
+    auto add = [&](int x, int y, int z) {
+      for (const auto& e : u)
+        if (e[0] == x && e[1] == y && e[2] == z) return;
+      u.push_back({x, y, z});
+    };
+    add(0, 0, 0);
+    add(d.x, d.y, d.z);
+    for (int t = 0; t < lp.total; ++t) {
+      const ShellVec v = shell_vec(kind, t);
+      add(v.x, v.y, v.z);
+    }
+    for (int t = 0; t < lp.total; ++t) {
+      const ShellVec v = shell_vec(kind, t);
+      add(d.x + v.x, d.y + v.y, d.z + v.z);
+    }
+    lp.n_u[dir] = static_cast<int>(u.size());
+    for (size_t e = 0; e < u.size(); ++e) {
+      for (int c = 0; c < 3; ++c) lp.u[dir][e][c] = static_cast<int8_t>(u[e][c]);
+      // shells of site k = i + u holding i (vector -u) and j (vector d - u);
+      // with n_d >= 4 no two of these displacements name the same site
+      for (int m = 0; m < lp.M; ++m)
+        for (int t = shell_start(kind, m); t < shell_start(kind, m + 1); ++t) {
+          const ShellVec v = shell_vec(kind, t);
+          if (v.x == -u[e][0] && v.y == -u[e][1] && v.z == -u[e][2])
+            lp.shells_i[dir][e] |= static_cast<uint8_t>(1u << m);
+          if (v.x == d.x - u[e][0] && v.y == d.y - u[e][1] && v.z == d.z - u[e][2])
+            lp.shells_j[dir][e] |= static_cast<uint8_t>(1u << m);
+        }
+    }
+  }
+  SMCX_CUDA(lat, cudaMemcpyAsync(lat->dlp(), &lp, sizeof(lp), cudaMemcpyHostToDevice, lat->stream));
+  SMCX_CUDA(lat, cudaMemcpyAsync(lat->dT(), t_q, sizeof(int64_t) * n_T, cudaMemcpyHostToDevice,
+                                 lat->stream));
+  SMCX_CUDA(lat, cudaStreamSynchronize(lat->stream));
+  lat->M = n_shells;
+  lat->local = true;
+  lat->zt = static_cast<int>(zt);
+  lat->n_T = static_cast<int>(n_T);
+  lat->V.clear();
+  lat->tiled_table_ok = false;
+  lat->has_epi = true;
+  compute_layout(lat);
+  tuning_reset(lat);
+  return restart_running_energy(lat);
 }
 
 constexpr int kTuneSamples = 3;  // timed phases per candidate
@@ -1069,6 +1212,7 @@ smcx_status smcx_checkpoint(smcx_lattice* lat, void* buf, size_t* len) {
   smcx_status s = check_handle(lat);
   if (s != SMCX_OK) return s;
   if (!len) return fail(SMCX_EINVAL, "null len");
+  if (lat->local) return fail(SMCX_ESTATE, "checkpoints hold EPI lattices only");
   const size_t K = lat->desc.n_species;
   const size_t need = 8 + sizeof(smcx_lattice_desc) + 4 + 4 + 8 + sizeof(int64_t) * lat->M * K * K +
                       lat->N + 4;

@@ -216,4 +216,29 @@ struct ShellParam {
   int start[kMaxShells + 1];
 };
 
+// Local-energy model (the nonlinear short-range model of Sec. 3): per-site
+// energies eps(i) = sum_m sum_s T_m[s_i][s][c_{i,m,s}] of the shell-resolved
+// species counts, at most 3 shells and 8 species.  A trial recomputes eps on
+// every distinct site of U = {i, j} u shells(i) u shells(j); u[dir] lists
+// those sites as displacements from i (half units) for partner direction dir,
+// which are distinct sites when every n_d >= 4.
+constexpr int kLocalMaxShells = 3;
+constexpr int kLocalMaxK = 8;
+constexpr int kLocalMaxV = 42;                // FCC shells 1-3: 12 + 6 + 24
+constexpr int kLocalMaxU = 2 + 2 * kLocalMaxV;
+constexpr int kLocalMaxZ1 = 12;
+constexpr int kLocalMaxZT = 25;               // 1 + the largest z_m in use
+constexpr int64_t kLocalMaxAbsT = int64_t(1) << 48;
+// u[dir][0] = 0 (the site i) and u[dir][1] = the partner j; for the others,
+// shells_i / shells_j: bit m set when i / j is in shell m+1 of that site.
+struct LocalParam {
+  int M, K, zt, total;
+  int start[kLocalMaxShells + 1];
+  int n_u[kLocalMaxZ1];
+  int8_t v[kLocalMaxV][3];
+  int8_t u[kLocalMaxZ1][kLocalMaxU][3];
+  uint8_t shells_i[kLocalMaxZ1][kLocalMaxU];
+  uint8_t shells_j[kLocalMaxZ1][kLocalMaxU];
+};
+
 }  // namespace smcx

@@ -51,6 +51,30 @@ def epi_table(n_shells: int, K: int, sigma_ev: float, seed: int) -> np.ndarray:
     return V
 
 
+# coordination numbers of shells 1-3 (BCC 8, 6, 12; FCC 12, 6, 24)
+_Z = {0: (8, 6, 12), 1: (12, 6, 24)}
+
+
+def local_energy_table(kind: int, n_shells: int, K: int, sigma_ev: float, seed: int) -> np.ndarray:
+    """Synthetic table of the local-energy model: T[m][a][s][c] = c V_m(a,s) / 2
+    + U_m(a,s) c^2 / z_m (q units, [M][K][K][1 + max z_m]), V from epi_table
+    and U ~ N(0, sigma/4) per (m, a, s) from the same seed: a pairwise part
+    plus a term quadratic in each shell count, so the energy is a nonlinear
+    function of the local order around every site."""
+    z = _Z[kind][:n_shells]
+    zt = 1 + max(z)
+    V = epi_table(n_shells, K, sigma_ev, seed)
+    rng = np.random.Generator(np.random.PCG64(seed + 7919))
+    U = rng.normal(0.0, sigma_ev / 4.0, (n_shells, K, K))
+    c = np.arange(zt, dtype=np.float64)
+    T = np.zeros((n_shells, K, K, zt), dtype=np.int64)
+    for m in range(n_shells):
+        quad = U[m][:, :, None] * c[None, None, :] ** 2 / z[m]
+        T[m] = (V[m][:, :, None] // 2) * np.arange(zt, dtype=np.int64)[None, None, :] + \
+            np.rint(quad * Q_PER_EV).astype(np.int64)
+    return T
+
+
 def composition_counts(N: int, K: int, fractions=None) -> np.ndarray:
     if fractions is None:
         base = N // K

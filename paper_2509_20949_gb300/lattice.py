@@ -15,7 +15,7 @@ from ._lib import LatticeDesc, SweepStats, check
 BCC, FCC = 0, 1
 NO_SHIFT, SINGLE_CELL = 1, 2
 OPT_KERNEL, OPT_TILE = 1, 2
-KERNEL_AUTO, KERNEL_GENERIC, KERNEL_TILED = 0, 1, 2
+KERNEL_AUTO, KERNEL_GENERIC, KERNEL_TILED, KERNEL_CELL, KERNEL_LOCAL = 0, 1, 2, 3, 4
 
 
 def make_desc(kind, n, n_species, pack_bits=8, min_cell=0, flags=0, seed=0) -> LatticeDesc:
@@ -28,6 +28,11 @@ def make_desc(kind, n, n_species, pack_bits=8, min_cell=0, flags=0, seed=0) -> L
     d.flags = int(flags)
     d.seed = int(seed)
     return d
+
+
+def local_model_width(kind, n_shells) -> int:
+    """Count-axis length of a local-energy table (1 + max z_m), 0 if invalid."""
+    return int(_lib.lib().smcx_local_model_width(int(kind), int(n_shells)))
 
 
 def _host_ptr(a: np.ndarray):
@@ -68,6 +73,7 @@ class Lattice:
                                              ctypes.byref(h)))
         self.h = h
         self.M = 0
+        self.local_model = False
 
     # ------------------------------------------------------------------
     def close(self):
@@ -87,6 +93,21 @@ class Lattice:
             raise ValueError("EPI table must be [M][K][K]")
         check(self.L.smcx_set_epi(self.h, V.shape[0], _host_ptr(V)))
         self.M = V.shape[0]
+        self.local_model = False
+
+    def set_local_model(self, T):
+        """Local-energy model (the nonlinear short-range model of Sec. 3):
+        T is [M][K][K][zt] int64 q units, T[m][a][s][c] = energy of a site of
+        species a whose shell m+1 holds c sites of species s
+        (zt = local_model_width(kind, M))."""
+        T = np.ascontiguousarray(T, dtype=np.int64)
+        if T.ndim != 4 or T.shape[1] != self.K or T.shape[2] != self.K:
+            raise ValueError("local-energy table must be [M][K][K][zt]")
+        if T.shape[3] != local_model_width(self.kind, T.shape[0]):
+            raise ValueError("local-energy table: wrong count axis length")
+        check(self.L.smcx_set_local_model(self.h, T.shape[0], _host_ptr(T)))
+        self.M = T.shape[0]
+        self.local_model = True
 
     def set_option(self, key, value):
         check(self.L.smcx_set_option(self.h, int(key), int(value)))

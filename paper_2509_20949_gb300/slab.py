@@ -76,6 +76,9 @@ class SlabSweep:
             self.world, self.rank, self.device_comm = 1, 0, False
         if not lattice.M:
             raise ValueError("set the lattice's EPI before decomposing it")
+        if getattr(lattice, "local_model", False):
+            raise ValueError("the z decomposition plans EPI link cells; the local-energy "
+                             "model's cells are larger")
         self.n_z = int(lattice.desc.n[2])
         plan(lattice.desc, lattice.M, self.world, self.rank, 0)  # raises if the split is invalid
 

@@ -96,3 +96,10 @@ def test_batch_tile_shapes(L):
     # options of a null batch are refused without a device
     assert L.smcx_batch_set_option(None, 1, 0) == _lib.SMCX_EINVAL
     assert L.smcx_batch_tuning(None, None, None, None, None) == _lib.SMCX_EINVAL
+
+
+def test_local_model_width_agrees_with_oracle(L, orc):
+    for kind in (0, 1):
+        for M in (1, 2, 3):
+            assert L.smcx_local_model_width(kind, M) == orc.local_width(kind, M)
+    assert L.smcx_local_model_width(0, 4) == 0 and L.smcx_local_model_width(2, 1) == 0

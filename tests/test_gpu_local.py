@@ -1,0 +1,99 @@
+"""The local-energy model on the GPU (the nonlinear short-range model of
+Sec. 3): trajectories, statistics and energies equal the oracle's bit for bit
+(every kernel trial recomputes the local energies of its interaction zone,
+like the oracle's); the linear table reproduces the EPI sweep on the same
+link cells; invalid uses are refused."""
+import numpy as np
+import pytest
+
+from paper_2509_20949_gb300 import inputs
+from tests.gpu_util import gpu_lattice, make_case, oracle_desc, require_cuda
+
+pytestmark = pytest.mark.gpu
+
+SCHEDULE = [(2, 1500.0, 800.0), (2, 600.0, 600.0), (1, float("inf"), float("inf")),
+            (1, 0.0, 0.0)]
+
+
+def _table(kind, M, K, seed, scale=0.02):
+    from paper_2509_20949_gb300.lattice import local_model_width
+    zt = local_model_width(kind, M)
+    rng = np.random.default_rng(seed)
+    return np.round(rng.normal(0.0, scale, (M, K, K, zt)) * 2.0 ** 32).astype(np.int64)
+
+
+@pytest.mark.parametrize("kind,n,K,M,pack", [
+    (0, (12, 9, 10), 4, 3, 8),   # BCC shells 1-3, ragged cells
+    (1, (8, 7, 9), 5, 3, 8),     # FCC shells 1-3
+    (0, (9, 12, 7), 3, 2, 4),    # 4-bit storage
+    (1, (6, 6, 13), 8, 1, 8),    # K = 8, one shell
+    (0, (4, 5, 4), 2, 3, 8),     # n_d = 4: the smallest lattice, one cell along x and z
+])
+def test_local_sweeps_match_the_oracle(orc, kind, n, K, M, pack):
+    require_cuda()
+    case = make_case(kind, n, K, M, seed=31, occ_seed=32)
+    T = _table(kind, M, K, seed=33)
+    lat = gpu_lattice(case, pack_bits=pack)
+    lat.set_local_model(T)
+    assert lat.kernel_in_use()[0] == 4
+    d = oracle_desc(orc, case)
+    assert lat.layout() == orc.local_layout(d)
+    occ = case["occ"]
+    E0 = orc.local_energy(d, T, occ)
+    assert lat.energy() == E0 == lat.running_energy()
+    t = 0
+    for nsw, a, b in SCHEDULE:
+        st = lat.sweep(nsw, a, b)
+        occ, per = orc.local_sweeps(d, T, occ, t, nsw, a, b)
+        t += nsw
+        assert np.array_equal(lat.occupancy(), occ), (nsw, a)
+        for key in ("attempts", "unlike", "accepted", "sum_dE"):
+            assert st[key] == int(per[key].sum()), key
+    assert lat.energy() == orc.local_energy(d, T, occ) == lat.running_energy()
+
+
+def test_linear_table_is_the_epi_sweep_on_the_same_cells(orc):
+    require_cuda()
+    from paper_2509_20949_gb300.lattice import local_model_width
+    kind, n, K, M = 0, (14, 12, 12), 5, 3
+    V = (inputs.epi_table(M, K, 0.03, 5) // 2) * 2
+    c = np.arange(local_model_width(kind, M), dtype=np.int64)
+    T = (V[:, :, :, None] // 2) * c[None, None, None, :]
+    case = make_case(kind, n, K, M, seed=7)
+    loc = gpu_lattice(case)
+    loc.set_local_model(T)
+    L, _ = loc.layout()
+    epi_case = dict(case, V=V, min_cell=L)
+    epi = gpu_lattice(epi_case)
+    assert epi.layout() == loc.layout()
+    assert loc.energy() == epi.energy()
+    for nsw, a, b in SCHEDULE[:3]:
+        assert loc.sweep(nsw, a, b) == epi.sweep(nsw, a, b)
+    assert np.array_equal(loc.occupancy(), epi.occupancy())
+
+
+def test_refusals_and_switching_back(orc):
+    require_cuda()
+    from paper_2509_20949_gb300 import SmcxError
+    from paper_2509_20949_gb300.lattice import local_model_width
+    assert local_model_width(0, 4) == 0 and local_model_width(2, 1) == 0
+    assert local_model_width(0, 3) == 13 and local_model_width(1, 3) == 25
+    big_k = gpu_lattice(make_case(0, (6, 6, 6), 9, 2))
+    with pytest.raises(SmcxError):
+        big_k.set_local_model(_table(0, 2, 9, 1))
+    thin = gpu_lattice(make_case(1, (6, 3, 6), 3, 2))
+    with pytest.raises(SmcxError):
+        thin.set_local_model(_table(1, 2, 3, 1))
+    case = make_case(0, (8, 8, 8), 3, 2, seed=3)
+    lat = gpu_lattice(case)
+    huge = _table(0, 2, 3, 1)
+    huge[0, 0, 0, 0] = 1 << 50
+    with pytest.raises(SmcxError):
+        lat.set_local_model(huge)
+    lat.set_local_model(_table(0, 2, 3, 2))
+    with pytest.raises(SmcxError):
+        lat.checkpoint()
+    lat.sweep(2, 900.0)
+    lat.set_epi(case["V"])
+    assert lat.kernel_in_use()[0] != 4
+    assert lat.energy() == orc.energy(oracle_desc(orc, case), case["V"], lat.occupancy())
