@@ -114,7 +114,7 @@ cudaError_t launch_merge_planes(uint8_t* occ, const uint8_t* theirs, const uint8
 // are device copies (T: [M][K][K][zt] int64, n_T entries).
 cudaError_t launch_sweep_local(const Geom& g, const PhaseArgs& a, const Tables& tab,
                                uint8_t* occ, const LocalParam* lp, const int64_t* T, int n_T,
-                               unsigned long long* stats, cudaStream_t st);
+                               int n_items, unsigned long long* stats, cudaStream_t st);
 cudaError_t launch_local_energy(const Geom& g, const LocalParam* lp, const int64_t* T, int n_T,
                                 const uint8_t* occ, long long* partial, int n_blocks,
                                 cudaStream_t st);

@@ -4,6 +4,7 @@
 // device storage.  In the sweep, one thread runs all trials of one link cell
 // of the active colour (Sec. 2.2: cells of one colour never interact);
 // every neighbour is located from coordinates with periodic wrap.
+#include <cstddef>
 #include <type_traits>
 #include "device_util.cuh"
 #include "kernels.h"
@@ -464,19 +465,41 @@ __device__ __forceinline__ int64_t local_bystander_change(const Geom& g, const L
   return de;
 }
 
-constexpr int kLocalParamBytes = (sizeof(LocalParam) + 15) / 16 * 16;
+// the part of LocalParam the kernels keep in shared memory (the item lists
+// are read once per block)
+constexpr int kLocalParamCopy = (offsetof(LocalParam, item_e) + 3) / 4 * 4;
+constexpr int kLocalParamBytes = (kLocalParamCopy + 15) / 16 * 16;
+
+// Fast path of the local kernel (8-bit storage, a cell whose sites and their
+// reads, up to 3 conventional cells away, do not cross the periodic seam):
+// every site is a byte address in device storage and a displacement adds a
+// fixed delta for a given basis.  Per block: dv[b][t] / bv[b][t] = delta and
+// basis reached by shell vector t from a basis-b site, du[b][dir][e] /
+// di[b][dir][x] / bi[b][dir][x] the same for the site of item x, and
+// im[dir][x] its shell and sign; sized for the lattice's basis count,
+// first-shell size and item count (the unified L1 keeps the rest).
+__host__ __device__ inline int local_fast_bytes(int nb, int z1, int n_items) {
+  return 5 * nb * kLocalMaxV + 5 * nb * z1 * n_items + z1 * n_items;
+}
+
+__device__ __forceinline__ int fast_delta(const Geom& g, int b, int dx, int dy, int dz, int* bn) {
+  const int hx = basis_comp(g.kind, b, 0) + dx, hy = basis_comp(g.kind, b, 1) + dy,
+            hz = basis_comp(g.kind, b, 2) + dz;
+  *bn = basis_of_parity(g.kind, hx & 1, hy & 1, hz & 1);
+  const int plane = g.n[1] * g.px;
+  return (*bn - b) * (g.n[2] * plane) + (hz >> 1) * plane + (hy >> 1) * g.px + (hx >> 1);
+}
 
 __device__ void load_local(unsigned char* smem, const LocalParam* lp_g, const int64_t* T_g,
                            int n_T) {
   const uint32_t* src = reinterpret_cast<const uint32_t*>(lp_g);
   uint32_t* dst = reinterpret_cast<uint32_t*>(smem);
-  for (int w = threadIdx.x; w < static_cast<int>(sizeof(LocalParam) / 4); w += blockDim.x)
-    dst[w] = src[w];
+  for (int w = threadIdx.x; w < kLocalParamCopy / 4; w += blockDim.x) dst[w] = src[w];
   int64_t* t = reinterpret_cast<int64_t*>(smem + kLocalParamBytes);
   for (int w = threadIdx.x; w < n_T; w += blockDim.x) t[w] = T_g[w];
 }
 
-__global__ void __launch_bounds__(128) k_sweep_local(const __grid_constant__ Geom g,
+__global__ void __launch_bounds__(128, 6) k_sweep_local(const __grid_constant__ Geom g,
                                                     const PhaseArgs a,
                                                     const __grid_constant__ Tables tab,
                                                     uint8_t* __restrict__ occ,
@@ -489,9 +512,39 @@ __global__ void __launch_bounds__(128) k_sweep_local(const __grid_constant__ Geo
   load_local(smem, lp_g, T_g, n_T);
   uint32_t* s_tab = reinterpret_cast<uint32_t*>(smem + kLocalParamBytes + 8 * n_T);
   for (int w = threadIdx.x; w < kTabWords; w += blockDim.x) s_tab[w] = tab.w[w];
+  const int n_items = lp_g->n_items;
+  int* dv = reinterpret_cast<int*>(s_tab + kTabWords);
+  int* di = dv + g.nb * kLocalMaxV;
+  uint8_t* bv = reinterpret_cast<uint8_t*>(di + g.nb * g.z1 * n_items);
+  uint8_t* bi = bv + g.nb * kLocalMaxV;
+  uint8_t* im = bi + g.nb * g.z1 * n_items;
+  // the fast path needs 8-bit storage and byte addresses (hence deltas) that
+  // fit int32
+  const bool fast_ok = !g.pack4 && static_cast<int64_t>(g.nb) * g.n[2] * g.n[1] * g.px < (1ll << 31);
   __syncthreads();
   const LocalParam& lp = *reinterpret_cast<const LocalParam*>(smem);
   const int64_t* T = reinterpret_cast<const int64_t*>(smem + kLocalParamBytes);
+  if (fast_ok) {
+    for (int w = threadIdx.x; w < g.nb * lp.total; w += blockDim.x) {
+      const int b = w / lp.total, t = w % lp.total;
+      int bn;
+      dv[b * kLocalMaxV + t] = fast_delta(g, b, lp.v[t][0], lp.v[t][1], lp.v[t][2], &bn);
+      bv[b * kLocalMaxV + t] = static_cast<uint8_t>(bn);
+    }
+    const int n_dir = g.z1 * n_items;
+    for (int w = threadIdx.x; w < g.nb * n_dir; w += blockDim.x) {
+      const int b = w / n_dir, r = w % n_dir, dir = r / n_items, x = r % n_items;
+      const int e = lp_g->item_e[dir][x];
+      int bn;
+      di[w] = fast_delta(g, b, lp.u[dir][e][0], lp.u[dir][e][1], lp.u[dir][e][2], &bn);
+      bi[w] = static_cast<uint8_t>(bn);
+      if (b == 0) im[r] = lp_g->item_m[dir][x];
+    }
+  }
+  __syncthreads();
+  // species of a stored code sigma * W: exact multiply-shift
+  const uint32_t invW = (65536u + static_cast<uint32_t>(g.W) - 1u) / static_cast<uint32_t>(g.W);
+  const int K = lp.K, zt = lp.zt;
 
   uint64_t att = 0, unl = 0, acc = 0;
   int64_t sum_de = 0;
@@ -510,6 +563,14 @@ __global__ void __launch_bounds__(128) k_sweep_local(const __grid_constant__ Geo
       lo[d] = static_cast<int>((static_cast<int64_t>(c[d]) * g.n[d]) / g.m[d]);
       hi[d] = static_cast<int>((static_cast<int64_t>(c[d] + 1) * g.n[d]) / g.m[d]);
     }
+    // every site of the cell and every site its trials read, within 3
+    // conventional cells, stays clear of the periodic seam
+    bool fast = fast_ok;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      const int x0 = pmod(lo[d] + a.shift[d], g.n[d]);
+      fast = fast && x0 >= 3 && x0 + (hi[d] - lo[d]) + 3 <= g.n[d];
+    }
     uint32_t k = 0;
     U4 w = {0, 0, 0, 0};
     for (int zs = lo[2]; zs < hi[2]; ++zs)
@@ -525,6 +586,72 @@ __global__ void __launch_bounds__(128) k_sweep_local(const __grid_constant__ Geo
             const uint32_t wa = (k & 1u) ? w.z : w.x;
             const uint32_t wb = (k & 1u) ? w.w : w.y;
             const uint32_t dir = __umulhi(wa, static_cast<uint32_t>(g.z1));
+            if (fast) {
+              ++att;
+              const int ai = static_cast<int>(dev_row(g, b, si.z, si.y)) + si.x;
+              const int aj = ai + dv[b * kLocalMaxV + dir];
+              const int bj = bv[b * kLocalMaxV + dir];
+              const uint32_t cp = occ[ai], cq = occ[aj];
+              if (cp == cq) continue;
+              ++unl;
+              const uint32_t p = (cp * invW) >> 16, q = (cq * invW) >> 16;
+              int64_t de = 0;
+              // i and j: every shell recounted before and after
+              auto full = [&](int ak, int bk, uint32_t cb, uint32_t ca) {
+                for (int m = 0; m < lp.M; ++m) {
+                  uint64_t nb_b = 0, nb_a = 0;
+                  for (int t = lp.start[m]; t < lp.start[m + 1]; ++t) {
+                    const int an = ak + dv[bk * kLocalMaxV + t];
+                    const uint32_t sb = (occ[an] * invW) >> 16;
+                    const uint32_t sa = an == ai ? q : (an == aj ? p : sb);
+                    nb_b += 1ull << (5 * sb);
+                    nb_a += 1ull << (5 * sa);
+                  }
+                  const int64_t* row_b = T + (static_cast<size_t>(m) * K + cb) * K * zt;
+                  const int64_t* row_a = T + (static_cast<size_t>(m) * K + ca) * K * zt;
+                  for (int s = 0; s < K; ++s)
+                    de += row_a[s * zt + count_field(nb_a, s)] - row_b[s * zt + count_field(nb_b, s)];
+                }
+              };
+              full(ai, b, p, q);
+              full(aj, bj, q, p);
+              // bystanders: item x scans the same shell for every lane
+              const int ib = (b * g.z1 + static_cast<int>(dir)) * n_items;
+              const uint8_t* imd = im + static_cast<int>(dir) * n_items;
+              for (int x = 0; x < n_items; ++x) {
+                const int ak = ai + di[ib + x], bk = bi[ib + x];
+                const int m = imd[x] & 3;
+                const int dp = (imd[x] >> 2) ? 1 : -1;  // i: p -> q; j: q -> p
+                const uint32_t c = (occ[ak] * invW) >> 16;
+                int np = 0, nq = 0;
+                for (int t = lp.start[m]; t < lp.start[m + 1]; ++t) {
+                  const uint32_t sn = occ[ak + dv[bk * kLocalMaxV + t]];
+                  np += sn == cp;
+                  nq += sn == cq;
+                }
+                const int64_t* row = T + (static_cast<size_t>(m) * K + c) * K * zt;
+                de += row[p * zt + np + dp] - row[p * zt + np] + row[q * zt + nq - dp] -
+                      row[q * zt + nq];
+              }
+              bool accept;
+              if (de <= 0 || a.mode == kModeAcceptAll) {
+                accept = true;
+              } else if (a.mode == kModeZeroT) {
+                accept = false;
+              } else {
+                const uint64_t idx = static_cast<uint64_t>(de) >> a.s;
+                accept = idx < (1ull << 27) &&
+                         wb < compose_threshold(s_tab[idx & 511u], s_tab[512 + ((idx >> 9) & 511u)],
+                                                s_tab[1024 + (idx >> 18)]);
+              }
+              if (accept) {
+                occ[ai] = static_cast<uint8_t>(cq);
+                occ[aj] = static_cast<uint8_t>(cp);
+                ++acc;
+                sum_de += de;
+              }
+              continue;
+            }
             const SiteXYZ sj = neighbour_near(g, si, lp.v[dir][0], lp.v[dir][1], lp.v[dir][2]);
             const uint32_t p = occ_get(g, occ, si), q = occ_get(g, occ, sj);
             ++att;
@@ -612,7 +739,7 @@ size_t local_smem_bytes(int n_T) { return kLocalParamBytes + 8 * static_cast<siz
 
 cudaError_t launch_sweep_local(const Geom& g, const PhaseArgs& a, const Tables& tab,
                                uint8_t* occ, const LocalParam* lp, const int64_t* T, int n_T,
-                               unsigned long long* stats, cudaStream_t st) {
+                               int n_items, unsigned long long* stats, cudaStream_t st) {
   uint32_t cnt[2];
   for (int d = 0; d < 2; ++d) {
     if (g.m[d] == 1 && ((a.colour >> d) & 1)) return cudaSuccess;
@@ -620,7 +747,7 @@ cudaError_t launch_sweep_local(const Geom& g, const PhaseArgs& a, const Tables& 
   }
   if (a.naz <= 0) return cudaErrorInvalidValue;
   const uint32_t n_active = cnt[0] * cnt[1] * static_cast<uint32_t>(a.naz);
-  const size_t smem = local_smem_bytes(n_T) + 4 * kTabWords;
+  const size_t smem = local_smem_bytes(n_T) + 4 * kTabWords + local_fast_bytes(g.nb, g.z1, n_items);
   cudaError_t e = cudaFuncSetAttribute(k_sweep_local, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        static_cast<int>(smem));
   if (e != cudaSuccess) return e;

@@ -214,6 +214,7 @@ struct smcx_lattice {
   bool local = false;           // the local-energy model replaces the EPI model
   int zt = 0;                   // its table's count axis
   int n_T = 0;                  // its table's entries
+  int n_items = 0;              // its bystander (site, shell) items per direction
   int tiled_kmax = 0;
   // online kernel choice (SMCX_OPT_KERNEL = 0 and SMCX_OPT_TILE = -1): the
   // candidates (kernel, tile shape), the fastest phase seen for each, and
@@ -562,7 +563,7 @@ smcx_status launch_colour_with(smcx_lattice* lat, int colour, const PhaseArgs& b
     return fail(SMCX_EINVAL, "the requested kernel does not support this lattice/EPI/tile shape");
   if (kern == 4) {
     SMCX_CUDA(lat, launch_sweep_local(g, a, tab, lat->d_occ, lat->dlp(), lat->dT(), lat->n_T,
-                                      lat->stats(), lat->stream));
+                                      lat->n_items, lat->stats(), lat->stream));
     return SMCX_OK;
   }
   if (kern == 3) {
@@ -836,6 +837,24 @@ smcx_status smcx_set_local_model(smcx_lattice* lat, uint32_t n_shells, const int
         }
     }
   }
+  // the items: (e, m) with exactly one of i, j in shell m+1 of site e, by shell
+  for (int dir = 0; dir < z1; ++dir) {
+    int n = 0;
+    for (int m = 0; m < lp.M; ++m)
+      for (int e = 2; e < lp.n_u[dir]; ++e) {
+        const uint32_t mi = (lp.shells_i[dir][e] >> m) & 1u, mj = (lp.shells_j[dir][e] >> m) & 1u;
+        if (mi == mj) continue;
+        if (n >= kLocalMaxItems) return fail(SMCX_EINVAL, "internal: local item list overflow");
+        lp.item_e[dir][n] = static_cast<uint8_t>(e);
+        lp.item_m[dir][n] = static_cast<uint8_t>(m | (mj << 2));
+        ++n;
+      }
+    if (dir == 0) lp.n_items = n;
+    if (n != lp.n_items) return fail(SMCX_EINVAL, "internal: directions differ in item count");
+    for (int x = 0; x < n; ++x)
+      if ((lp.item_m[dir][x] & 3) != (lp.item_m[0][x] & 3))
+        return fail(SMCX_EINVAL, "internal: directions differ in item shells");
+  }
   SMCX_CUDA(lat, cudaMemcpyAsync(lat->dlp(), &lp, sizeof(lp), cudaMemcpyHostToDevice, lat->stream));
   SMCX_CUDA(lat, cudaMemcpyAsync(lat->dT(), t_q, sizeof(int64_t) * n_T, cudaMemcpyHostToDevice,
                                  lat->stream));
@@ -844,6 +863,7 @@ smcx_status smcx_set_local_model(smcx_lattice* lat, uint32_t n_shells, const int
   lat->local = true;
   lat->zt = static_cast<int>(zt);
   lat->n_T = static_cast<int>(n_T);
+  lat->n_items = lp.n_items;
   lat->V.clear();
   lat->tiled_table_ok = false;
   lat->has_epi = true;

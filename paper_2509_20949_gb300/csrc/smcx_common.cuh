@@ -231,14 +231,24 @@ constexpr int kLocalMaxZT = 25;               // 1 + the largest z_m in use
 constexpr int64_t kLocalMaxAbsT = int64_t(1) << 48;
 // u[dir][0] = 0 (the site i) and u[dir][1] = the partner j; for the others,
 // shells_i / shells_j: bit m set when i / j is in shell m+1 of that site.
+// The items list, per direction, every (site e of U, shell m+1) in which
+// exactly one of i, j lies, sorted by shell: item_m = m | (j's shell) << 2.
+// Every direction has the same items per shell (the directions are images of
+// one another under the point group), so item x scans the same shell for
+// every direction.
+constexpr int kLocalMaxItems = 2 * kLocalMaxU;
 struct LocalParam {
   int M, K, zt, total;
   int start[kLocalMaxShells + 1];
   int n_u[kLocalMaxZ1];
+  int n_items;
   int8_t v[kLocalMaxV][3];
   int8_t u[kLocalMaxZ1][kLocalMaxU][3];
   uint8_t shells_i[kLocalMaxZ1][kLocalMaxU];
   uint8_t shells_j[kLocalMaxZ1][kLocalMaxU];
+  // not copied to shared memory by the sweep kernel (read once per block)
+  uint8_t item_e[kLocalMaxZ1][kLocalMaxItems];
+  uint8_t item_m[kLocalMaxZ1][kLocalMaxItems];
 };
 
 }  // namespace smcx

@@ -97,3 +97,24 @@ def test_refusals_and_switching_back(orc):
     lat.set_epi(case["V"])
     assert lat.kernel_in_use()[0] != 4
     assert lat.energy() == orc.energy(oracle_desc(orc, case), case["V"], lat.occupancy())
+
+
+@pytest.mark.parametrize("kind,n,K,M", [(0, (22, 20, 24), 5, 3), (1, (16, 15, 17), 4, 3)])
+def test_interior_cells_match_the_oracle(orc, kind, n, K, M):
+    """Lattices large enough that most cells run the seam-free fast path
+    (byte-address deltas), next to the seam cells on the general path."""
+    require_cuda()
+    case = make_case(kind, n, K, M, seed=41, occ_seed=42)
+    T = _table(kind, M, K, seed=43)
+    lat = gpu_lattice(case)
+    lat.set_local_model(T)
+    d = oracle_desc(orc, case)
+    occ = case["occ"]
+    t = 0
+    for nsw, a, b in SCHEDULE[:2]:
+        st = lat.sweep(nsw, a, b)
+        occ, per = orc.local_sweeps(d, T, occ, t, nsw, a, b)
+        t += nsw
+        assert np.array_equal(lat.occupancy(), occ)
+        assert st["accepted"] == int(per["accepted"].sum()) and st["sum_dE"] == int(per["sum_dE"].sum())
+    assert lat.running_energy() == lat.energy() == orc.local_energy(d, T, occ)
