@@ -4,6 +4,7 @@
 // device storage.  In the sweep, one thread runs all trials of one link cell
 // of the active colour (Sec. 2.2: cells of one colour never interact);
 // every neighbour is located from coordinates with periodic wrap.
+#include <vector>
 #include <cstddef>
 #include <type_traits>
 #include "device_util.cuh"
@@ -482,6 +483,47 @@ __host__ __device__ inline int local_fast_bytes(int nb, int z1, int n_items) {
   return 5 * nb * kLocalMaxV + 5 * nb * z1 * n_items + z1 * n_items;
 }
 
+// Order of the cells of one launch: the interior cells (the product of one
+// circular run of active cell indices per axis, a_d = (s0_d + i) mod A_d),
+// then the seam cells as three slabs, so that a warp's lanes take one path.
+// on = 0: plain raster order.
+struct LocalSplit {
+  int on;
+  int A[3], s0[3], I[3];
+};
+
+__device__ __forceinline__ void split_cell(const LocalSplit& sp, uint32_t tid, uint32_t* a) {
+  const uint32_t A0 = sp.A[0], A1 = sp.A[1], A2 = sp.A[2];
+  const uint32_t I0 = sp.I[0], I1 = sp.I[1], I2 = sp.I[2];
+  const uint32_t n_int = I0 * I1 * I2;
+  uint32_t i0, i1, i2;  // offsets from s0 along each axis
+  if (tid < n_int) {
+    i0 = tid % I0;
+    i1 = (tid / I0) % I1;
+    i2 = tid / (I0 * I1);
+  } else {
+    uint32_t r = tid - n_int;
+    const uint32_t S0 = A0 - I0, S1 = A1 - I1;
+    if (r < S0 * A1 * A2) {  // x seam: every y, z
+      i0 = I0 + r % S0;
+      i1 = (r / S0) % A1;
+      i2 = r / (S0 * A1);
+    } else if ((r -= S0 * A1 * A2) < I0 * S1 * A2) {  // y seam, x interior, every z
+      i0 = r % I0;
+      i1 = I1 + (r / I0) % S1;
+      i2 = r / (I0 * S1);
+    } else {  // z seam, x and y interior
+      r -= I0 * S1 * A2;
+      i0 = r % I0;
+      i1 = (r / I0) % I1;
+      i2 = I2 + r / (I0 * I1);
+    }
+  }
+  a[0] = (sp.s0[0] + i0) % A0;
+  a[1] = (sp.s0[1] + i1) % A1;
+  a[2] = (sp.s0[2] + i2) % A2;
+}
+
 __device__ __forceinline__ int fast_delta(const Geom& g, int b, int dx, int dy, int dz, int* bn) {
   const int hx = basis_comp(g.kind, b, 0) + dx, hy = basis_comp(g.kind, b, 1) + dy,
             hz = basis_comp(g.kind, b, 2) + dz;
@@ -507,7 +549,7 @@ __global__ void __launch_bounds__(128, 6) k_sweep_local(const __grid_constant__ 
                                                     const int64_t* __restrict__ T_g, int n_T,
                                                     unsigned long long* __restrict__ stats,
                                                     uint32_t n_active, uint32_t ax_n,
-                                                    uint32_t ay_n) {
+                                                    uint32_t ay_n, const LocalSplit split) {
   extern __shared__ __align__(16) unsigned char smem[];
   load_local(smem, lp_g, T_g, n_T);
   uint32_t* s_tab = reinterpret_cast<uint32_t*>(smem + kLocalParamBytes + 8 * n_T);
@@ -550,8 +592,18 @@ __global__ void __launch_bounds__(128, 6) k_sweep_local(const __grid_constant__ 
   int64_t sum_de = 0;
   const uint32_t tid = blockIdx.x * blockDim.x + threadIdx.x;
   if (tid < n_active) {
-    const uint32_t axi = tid % ax_n, ayi = (tid / ax_n) % ay_n,
-                   azi = tid / (ax_n * ay_n) + static_cast<uint32_t>(a.az0);
+    uint32_t axi, ayi, azi;
+    if (split.on) {
+      uint32_t av[3];
+      split_cell(split, tid, av);
+      axi = av[0];
+      ayi = av[1];
+      azi = av[2] + static_cast<uint32_t>(a.az0);
+    } else {
+      axi = tid % ax_n;
+      ayi = (tid / ax_n) % ay_n;
+      azi = tid / (ax_n * ay_n) + static_cast<uint32_t>(a.az0);
+    }
     const int c[3] = {
         g.m[0] == 1 ? 0 : static_cast<int>(2 * axi + (a.colour & 1)),
         g.m[1] == 1 ? 0 : static_cast<int>(2 * ayi + ((a.colour >> 1) & 1)),
@@ -751,8 +803,40 @@ cudaError_t launch_sweep_local(const Geom& g, const PhaseArgs& a, const Tables& 
   cudaError_t e = cudaFuncSetAttribute(k_sweep_local, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        static_cast<int>(smem));
   if (e != cudaSuccess) return e;
+  // interior cells first (a cell is interior when its sites and their reads,
+  // 3 conventional cells either way, stay clear of the periodic seam); the
+  // interior indices along each axis must form one circular run, else the
+  // plain order is kept (the kernel checks every cell itself either way)
+  LocalSplit sp{};
+  sp.on = !g.pack4 && static_cast<int64_t>(g.nb) * g.n[2] * g.n[1] * g.px < (1ll << 31);
+  const int Ad[3] = {static_cast<int>(cnt[0]), static_cast<int>(cnt[1]), a.naz};
+  for (int d = 0; d < 3 && sp.on; ++d) {
+    const int A = Ad[d], bit = (a.colour >> d) & 1;
+    std::vector<char> in(A);
+    int n_in = 0;
+    for (int i = 0; i < A; ++i) {
+      const int ai = d == 2 ? a.az0 + i : i;
+      const int c = g.m[d] == 1 ? 0 : 2 * ai + bit;
+      const int lo = static_cast<int>((static_cast<int64_t>(c) * g.n[d]) / g.m[d]);
+      const int hi = static_cast<int>((static_cast<int64_t>(c + 1) * g.n[d]) / g.m[d]);
+      int x0 = (lo + a.shift[d]) % g.n[d];
+      x0 += x0 < 0 ? g.n[d] : 0;
+      in[i] = x0 >= 3 && x0 + (hi - lo) + 3 <= g.n[d];
+      n_in += in[i];
+    }
+    int s0 = 0;
+    if (n_in > 0 && n_in < A)
+      for (int i = 0; i < A; ++i)
+        if (in[i] && !in[(i + A - 1) % A]) s0 = i;
+    int run = 0;
+    while (run < n_in && in[(s0 + run) % A]) ++run;
+    if (run != n_in) sp.on = 0;
+    sp.A[d] = A;
+    sp.s0[d] = s0;
+    sp.I[d] = n_in;
+  }
   k_sweep_local<<<(n_active + 127) / 128, 128, smem, st>>>(g, a, tab, occ, lp, T, n_T, stats,
-                                                          n_active, cnt[0], cnt[1]);
+                                                          n_active, cnt[0], cnt[1], sp);
   return cudaGetLastError();
 }
 
