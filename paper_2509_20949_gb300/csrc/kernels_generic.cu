@@ -466,9 +466,11 @@ __device__ __forceinline__ int64_t local_bystander_change(const Geom& g, const L
   return de;
 }
 
-// the part of LocalParam the kernels keep in shared memory (the item lists
-// are read once per block)
-constexpr int kLocalParamCopy = (offsetof(LocalParam, item_e) + 3) / 4 * 4;
+// the part of LocalParam the kernels keep in shared memory: counts, shell
+// ranges and shell vectors (the displacement lists of U, their shell masks
+// and the item lists are read from global memory, through L1: by the seam
+// path and once per block)
+constexpr int kLocalParamCopy = (offsetof(LocalParam, u) + 3) / 4 * 4;
 constexpr int kLocalParamBytes = (kLocalParamCopy + 15) / 16 * 16;
 
 // Fast path of the local kernel (8-bit storage, a cell whose sites and their
@@ -578,7 +580,7 @@ __global__ void __launch_bounds__(128, 6) k_sweep_local(const __grid_constant__ 
       const int b = w / n_dir, r = w % n_dir, dir = r / n_items, x = r % n_items;
       const int e = lp_g->item_e[dir][x];
       int bn;
-      di[w] = fast_delta(g, b, lp.u[dir][e][0], lp.u[dir][e][1], lp.u[dir][e][2], &bn);
+      di[w] = fast_delta(g, b, lp_g->u[dir][e][0], lp_g->u[dir][e][1], lp_g->u[dir][e][2], &bn);
       bi[w] = static_cast<uint8_t>(bn);
       if (b == 0) im[r] = lp_g->item_m[dir][x];
     }
@@ -714,10 +716,10 @@ __global__ void __launch_bounds__(128, 6) k_sweep_local(const __grid_constant__ 
             de += local_eps_change(g, lp, T, occ, si, p, q, ii, jj, p, q) +
                   local_eps_change(g, lp, T, occ, sj, q, p, ii, jj, p, q);
             for (int e = 2; e < lp.n_u[dir]; ++e) {
-              const uint32_t mi = lp.shells_i[dir][e], mj = lp.shells_j[dir][e];
+              const uint32_t mi = lp_g->shells_i[dir][e], mj = lp_g->shells_j[dir][e];
               if (mi == mj) continue;  // no shell holds exactly one of i, j
-              const SiteXYZ sk =
-                  neighbour_near(g, si, lp.u[dir][e][0], lp.u[dir][e][1], lp.u[dir][e][2]);
+              const SiteXYZ sk = neighbour_near(g, si, lp_g->u[dir][e][0], lp_g->u[dir][e][1],
+                                                lp_g->u[dir][e][2]);
               de += local_bystander_change(g, lp, T, occ, sk, occ_get(g, occ, sk), mi, mj, p, q);
             }
             bool accept;
