@@ -320,7 +320,9 @@ smcx_status smcx_restore(smcx_lattice* lat, const void* buf, size_t len);
                        2 = tiled (shared-memory tiles + halos, large lattices),
                        3 = cell (one thread per link cell, n_d >= 4)
                        (a sweep fails with EINVAL if the requested kernel
-                       cannot run the lattice)
+                       cannot run the lattice).  Under the local-energy
+                       model every sweep runs its own kernel, reported as 4
+                       by smcx_kernel_in_use, whatever this option says
      SMCX_OPT_TILE     index of the tile shape among smcx_tile_shape(...) */
 #define SMCX_OPT_KERNEL 1u
 #define SMCX_OPT_TILE 2u

@@ -517,6 +517,7 @@ void tuning_reset(smcx_lattice* lat) {
       if (tiled_supported(g, sh)) tu.cands.emplace_back(2, sh);
     if (cell_ok(lat)) tu.cands.emplace_back(3, -1);
   }
+  if (lat->local) tu.cands.emplace_back(4, -1);  // the local-energy model's one kernel
   if (tu.cands.empty()) tu.cands.emplace_back(1, -1);
   tu.best_ms.assign(tu.cands.size(), 0.0f);
   tu.samples.assign(tu.cands.size(), 0);

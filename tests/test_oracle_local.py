@@ -157,3 +157,14 @@ def test_single_cell_boltzmann_nonlinear_table(orc):
     Et = E0 + np.cumsum(st["sum_dE"].astype(np.int64))
     assert Et[-1] == orc.local_energy(d, T, o)
     _compare(levels, p, Et[500:])
+
+
+def test_synthetic_table_shape_and_zero_count(orc):
+    """inputs.local_energy_table: [M][K][K][1 + max z_m], no energy at a zero
+    count, and nonlinear in the count (a quadratic term on top of c V / 2)."""
+    for kind in (0, 1):
+        T = inputs.local_energy_table(kind, 3, 5, 0.02, seed=3)
+        assert T.shape == (3, 5, 5, orc.local_width(kind, 3)) and T.dtype == np.int64
+        assert np.all(T[..., 0] == 0)
+        lin = T[..., 1:2] * np.arange(T.shape[3])[None, None, None, :]
+        assert np.any(T != lin)
