@@ -254,6 +254,29 @@ def _job_arrays(j):
     return V, occ
 
 
+def cpu_baseline_local(w, M, seconds):
+    """The oracle's local-energy sweeps, single-threaded on the host, on a
+    bounded lattice of the workload's kind, composition and table recipe
+    (a full sweep of the benchmark lattice would take hours)."""
+    import oracle
+
+    n = 12
+    while True:
+        d = oracle.Desc(w["kind"], (n, n, n), w["K"], M, seed=w["seed"])
+        T = inputs.local_energy_table(w["kind"], M, w["K"], w["sigma"], w["epi_seed"])
+        occ = inputs.initial_occupancy(w["kind"], (n, n, n), w["K"], w["occ_seed"], w["fractions"])
+        t0 = time.perf_counter()
+        _, st = oracle.local_sweeps(d, T, occ, 0, 1, sweep_temperature(w, 0))
+        dt = time.perf_counter() - t0
+        if dt > seconds / 4 or n >= 48:
+            break
+        n = int(n * 1.5)
+    att = int(st["attempts"].sum())
+    return {"value": att / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"1 sweep of a {n}^3 lattice of the same kind, species, composition "
+                      f"and table recipe, {dt:.1f} s single-threaded"}
+
+
 def run_local(args):
     """The local-energy model (the nonlinear short-range model of Sec. 3): the
     workload's lattice and composition with a synthetic table (pairwise part
@@ -288,6 +311,10 @@ def run_local(args):
     t_ms = ev0.elapsed_time(ev1)
     ts = lat.sweep(1, sweep_temperature(w, args.warmup + args.steps))
     L, m = lat.layout()
+    peak, peak_src = measured_peaks()
+    phase_ms = t_ms / (args.steps * 8)
+    achieved = 2.0 * N / 8 / (phase_ms / 1e3) / 1e9  # 2 B per trial, as the EPI sweep
+    cpu = None if args.no_cpu_baseline else cpu_baseline_local(w, M, args.cpu_seconds)
     line = {"metric": "attempted MC swaps/sec on 1 GB300 (local-energy model)",
             "value": N * args.steps / (t_ms / 1e3), "unit": UNIT, "n_gpus": 1,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_ms / args.steps,
@@ -299,6 +326,12 @@ def run_local(args):
                        "pack_bits": args.pack_bits},
             "trial_stats": {"unlike_frac": ts["unlike"] / ts["attempts"],
                             "accepted_frac": ts["accepted"] / ts["attempts"]},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": None, "kernel": "local sweep phase",
+                         "kernel_ms_per_launch": phase_ms, "peak_source": peak_src,
+                         "limiter": {"unit": "L1/L2 load latency",
+                                     "source": "profiles/sweep_local_bcc448_k5.md"}},
+            "cpu_baseline": cpu,
             "clocks": clk, "gpu_launches": args.steps * 8}
     print(json.dumps(line), flush=True)
     return 0
