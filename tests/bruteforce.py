@@ -85,15 +85,15 @@ def pair_counts(kind, n, M, K, occ):
     return out
 
 
-def binary_energies(kind, n, V, configs):
-    """Energies of many binary configurations at once.  configs: [C, N] in
+def binary_energies(kind, n, V, states):
+    """Energies of many binary configurations at once.  states: [C, N] in
     {0,1}.  Uses the brute-force multiplicity matrices."""
     M = V.shape[0]
     mult = multiplicity(kind, n, M).astype(np.float64)
-    x = configs.astype(np.float64)
+    x = states.astype(np.float64)
     y = 1.0 - x
-    E = np.zeros(len(configs), dtype=np.float64)
-    exact = np.zeros(len(configs), dtype=object)
+    E = np.zeros(len(states), dtype=np.float64)
+    exact = np.zeros(len(states), dtype=object)
     for m in range(M):
         A = mult[m]
         xx = np.einsum("ci,ij,cj->c", x, A, x)
@@ -101,28 +101,28 @@ def binary_energies(kind, n, V, configs):
         xy = np.einsum("ci,ij,cj->c", y, A, x)
         yx = np.einsum("ci,ij,cj->c", x, A, y)
         # counts are exact small integers in float64
-        for c in range(len(configs)):
+        for c in range(len(states)):
             exact[c] += (int(round(yy[c])) * int(V[m, 0, 0]) + int(round(xx[c])) * int(V[m, 1, 1])
                          + (int(round(xy[c])) + int(round(yx[c]))) * int(V[m, 0, 1]))
-    for c in range(len(configs)):
+    for c in range(len(states)):
         assert exact[c] % 2 == 0
         exact[c] //= 2
     return exact
 
 
-def local_energies(kind, n, T, configs):
+def local_energies(kind, n, T, states):
     """Local-energy model E = sum_i sum_m sum_s T[m][s_i][s][c_{i,m,s}] of
-    many configurations (configs: [C, N] species ids), with the shell counts
+    many configurations (states: [C, N] species ids), with the shell counts
     c_{i,m,s} = sum_j mult_m(i, j) [s_j = s] taken from the brute-force
     multiplicity matrices (every periodic image counted).  Exact integers."""
     M, K = T.shape[0], T.shape[1]
-    configs = np.atleast_2d(np.asarray(configs, dtype=np.int64))
+    states = np.atleast_2d(np.asarray(states, dtype=np.int64))
     mult = multiplicity(kind, n, M)
-    onehot = (configs[:, :, None] == np.arange(K)[None, None, :]).astype(np.int64)  # [C, N, K]
-    out = np.zeros(len(configs), dtype=object)
+    onehot = (states[:, :, None] == np.arange(K)[None, None, :]).astype(np.int64)  # [C, N, K]
+    out = np.zeros(len(states), dtype=object)
     for m in range(M):
         cnt = np.einsum("ij,cjk->cik", mult[m], onehot)  # [C, N, K]
         for s in range(K):
-            vals = T[m][configs, s, cnt[:, :, s]]  # [C, N]
+            vals = T[m][states, s, cnt[:, :, s]]  # [C, N]
             out += np.array([int(v) for v in vals.astype(object).sum(1)], dtype=object)
     return out

@@ -65,13 +65,13 @@ def test_single_cell_bcc16(orc):
     n = (2, 2, 2)
     N = 16
     V = _binary_V(2, 31)
-    configs = np.array([[1 if i in c else 0 for i in range(N)]
+    states = np.array([[1 if i in c else 0 for i in range(N)]
                         for c in itertools.combinations(range(N), 8)], dtype=np.uint8)
-    E = bf.binary_energies(0, n, V, configs)
+    E = bf.binary_energies(0, n, V, states)
     T = 1500.0
     levels, p = _exact_levels(E, T)
     d = orc.Desc(0, n, 2, 2, seed=4, flags=orc.FLAG_SINGLE_CELL)
-    occ = configs[123].copy()
+    occ = states[123].copy()
     Et = _chain_levels(orc, d, V, occ, T, 120000)
     _compare(levels, p, Et)
 
@@ -81,16 +81,16 @@ def test_single_cell_fcc32_four_minority(orc):
     n = (2, 2, 2)
     N = 32
     V = _binary_V(2, 7, sigma=0.05)
-    configs = np.zeros((math.comb(N, 4), N), dtype=np.uint8)
+    states = np.zeros((math.comb(N, 4), N), dtype=np.uint8)
     for r, c in enumerate(itertools.combinations(range(N), 4)):
-        configs[r, list(c)] = 1
-    E = bf.binary_energies(1, n, V, configs)
+        states[r, list(c)] = 1
+    E = bf.binary_energies(1, n, V, states)
     T = 1200.0
     levels, p = _exact_levels(E, T)
     d = orc.Desc(1, n, 2, 2, seed=9)
     L, m = orc.layout(d)
     assert m == (1, 1, 1)
-    occ = configs[0].copy()
+    occ = states[0].copy()
     Et = _chain_levels(orc, d, V, occ, T, 60000)
     _compare(levels, p, Et)
 

@@ -145,13 +145,13 @@ def test_single_cell_boltzmann_nonlinear_table(orc):
     kind, n, M = 0, (2, 2, 2), 2
     N = 16
     T = _table(kind, M, 2, seed=17, scale=0.01)
-    configs = np.array([[1 if i in c else 0 for i in range(N)]
+    states = np.array([[1 if i in c else 0 for i in range(N)]
                         for c in itertools.combinations(range(N), 8)], dtype=np.uint8)
-    E = bf.local_energies(kind, n, T, configs)
+    E = bf.local_energies(kind, n, T, states)
     Temp = 1500.0
     levels, p = _exact_levels(E, Temp)
     d = orc.Desc(kind, n, 2, M, seed=4, flags=orc.FLAG_SINGLE_CELL)
-    occ = configs[321].copy()
+    occ = states[321].copy()
     E0 = orc.local_energy(d, T, occ)
     o, st = orc.local_sweeps(d, T, occ, 0, 60000, Temp)
     Et = E0 + np.cumsum(st["sum_dE"].astype(np.int64))
