@@ -118,3 +118,45 @@ def test_interior_cells_match_the_oracle(orc, kind, n, K, M):
         assert np.array_equal(lat.occupancy(), occ)
         assert st["accepted"] == int(per["accepted"].sum()) and st["sum_dE"] == int(per["sum_dE"].sum())
     assert lat.running_energy() == lat.energy() == orc.local_energy(d, T, occ)
+
+
+def test_colour_phases_over_plane_ranges_equal_the_sweep(orc):
+    """Cells of one colour never interact, so running each colour over
+    ranges of link-cell z planes (partial windows of the interior-first cell
+    order) gives the full sweep's bits."""
+    require_cuda()
+    case = make_case(0, (26, 18, 30), 4, 3, seed=51, occ_seed=52)
+    T = _table(0, 3, 4, seed=53)
+    a, b = gpu_lattice(case), gpu_lattice(case)
+    a.set_local_model(T)
+    b.set_local_model(T)
+    _, m = b.layout()
+    cuts = [0, 3, 4, m[2] - 2, m[2]]
+    for sweep in range(2):
+        temp = 900.0
+        sa = a.sweep(1, temp)
+        tot = dict(attempts=0, unlike=0, accepted=0, sum_dE=0)
+        for colour in range(8):
+            for lo, hi in zip(cuts, cuts[1:]):
+                st = b.run_colour_planes(colour, temp, lo, hi)
+                for k in tot:
+                    tot[k] += st[k]
+        b.sweep_counter = b.sweep_counter + 1
+        assert tot == sa
+        assert np.array_equal(a.occupancy(), b.occupancy())
+
+
+def test_bench_local_line(tmp_path):
+    require_cuda()
+    import json
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    r = subprocess.run([sys.executable, os.path.join(root, "bench.py"), "--mode", "local",
+                        "--workload", "bcc16_k4", "--steps", "3", "--warmup", "1",
+                        "--no-cpu-baseline"], cwd=root, capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0, r.stderr[-2000:]
+    line = json.loads([l for l in r.stdout.splitlines() if l.startswith("{")][-1])
+    assert line["mode"] == "local" and line["value"] > 0 and line["unit"] == "swaps/s"
+    assert line["roofline"]["bound"] == "hbm" and line["gpu_launches"] == 24
