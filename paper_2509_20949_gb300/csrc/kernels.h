@@ -112,9 +112,11 @@ cudaError_t launch_merge_planes(uint8_t* occ, const uint8_t* theirs, const uint8
 // local-energy model: one colour phase over cells z index az0 .. az0 + naz
 // (a.naz > 0), and the total energy as n_blocks int64 partial sums.  lp and T
 // are device copies (T: [M][K][K][zt] int64, n_T entries).
+// (t32: every table entry fits int32, and the kernel keeps the table in
+// shared memory as int32)
 cudaError_t launch_sweep_local(const Geom& g, const PhaseArgs& a, const Tables& tab,
                                uint8_t* occ, const LocalParam* lp, const int64_t* T, int n_T,
-                               int n_items, unsigned long long* stats, cudaStream_t st);
+                               bool t32, int n_items, unsigned long long* stats, cudaStream_t st);
 cudaError_t launch_local_energy(const Geom& g, const LocalParam* lp, const int64_t* T, int n_T,
                                 const uint8_t* occ, long long* partial, int n_blocks,
                                 cudaStream_t st);

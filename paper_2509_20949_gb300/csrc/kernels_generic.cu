@@ -415,9 +415,11 @@ __device__ __forceinline__ SiteXYZ neighbour_near(const Geom& g, const SiteXYZ& 
   return r;
 }
 
-// eps_after(k) - eps_before(k) for k = i or j (species cb before, ca after)
+// eps_after(k) - eps_before(k) for k = i or j (species cb before, ca after);
+// TT: the shared table's type (int32 when every entry fits, else int64)
+template <typename TT>
 __device__ __forceinline__ int64_t local_eps_change(const Geom& g, const LocalParam& lp,
-                                                    const int64_t* T, const uint8_t* occ,
+                                                    const TT* T, const uint8_t* occ,
                                                     const SiteXYZ& sk, uint32_t cb, uint32_t ca,
                                                     uint32_t ii, uint32_t jj, uint32_t p,
                                                     uint32_t q) {
@@ -433,18 +435,20 @@ __device__ __forceinline__ int64_t local_eps_change(const Geom& g, const LocalPa
       nb_b += 1ull << (5 * sb);
       nb_a += 1ull << (5 * sa);
     }
-    const int64_t* row_b = T + (static_cast<size_t>(m) * K + cb) * K * zt;
-    const int64_t* row_a = T + (static_cast<size_t>(m) * K + ca) * K * zt;
+    const TT* row_b = T + (static_cast<size_t>(m) * K + cb) * K * zt;
+    const TT* row_a = T + (static_cast<size_t>(m) * K + ca) * K * zt;
     for (int s = 0; s < K; ++s)
-      de += row_a[s * zt + count_field(nb_a, s)] - row_b[s * zt + count_field(nb_b, s)];
+      de += static_cast<int64_t>(row_a[s * zt + count_field(nb_a, s)]) -
+            static_cast<int64_t>(row_b[s * zt + count_field(nb_b, s)]);
   }
   return de;
 }
 
 // eps change of a site k other than i and j (species c): in each shell m+1
 // holding exactly one of them, the counts of p and q move by one
+template <typename TT>
 __device__ __forceinline__ int64_t local_bystander_change(const Geom& g, const LocalParam& lp,
-                                                          const int64_t* T, const uint8_t* occ,
+                                                          const TT* T, const uint8_t* occ,
                                                           const SiteXYZ& sk, uint32_t c,
                                                           uint32_t shells_i, uint32_t shells_j,
                                                           uint32_t p, uint32_t q) {
@@ -460,8 +464,9 @@ __device__ __forceinline__ int64_t local_bystander_change(const Geom& g, const L
       nq += sn == q;
     }
     const int dp = ((shells_i >> m) & 1u) ? -1 : 1;  // i: p -> q; j: q -> p
-    const int64_t* row = T + (static_cast<size_t>(m) * K + c) * K * zt;
-    de += row[p * zt + np + dp] - row[p * zt + np] + row[q * zt + nq - dp] - row[q * zt + nq];
+    const TT* row = T + (static_cast<size_t>(m) * K + c) * K * zt;
+    de += static_cast<int64_t>(row[p * zt + np + dp]) - row[p * zt + np] +
+          static_cast<int64_t>(row[q * zt + nq - dp]) - row[q * zt + nq];
   }
   return de;
 }
@@ -534,15 +539,17 @@ __device__ __forceinline__ int fast_delta(const Geom& g, int b, int dx, int dy, 
   return (*bn - b) * (g.n[2] * plane) + (hz >> 1) * plane + (hy >> 1) * g.px + (hx >> 1);
 }
 
+template <typename TT>
 __device__ void load_local(unsigned char* smem, const LocalParam* lp_g, const int64_t* T_g,
                            int n_T) {
   const uint32_t* src = reinterpret_cast<const uint32_t*>(lp_g);
   uint32_t* dst = reinterpret_cast<uint32_t*>(smem);
   for (int w = threadIdx.x; w < kLocalParamCopy / 4; w += blockDim.x) dst[w] = src[w];
-  int64_t* t = reinterpret_cast<int64_t*>(smem + kLocalParamBytes);
-  for (int w = threadIdx.x; w < n_T; w += blockDim.x) t[w] = T_g[w];
+  TT* t = reinterpret_cast<TT*>(smem + kLocalParamBytes);
+  for (int w = threadIdx.x; w < n_T; w += blockDim.x) t[w] = static_cast<TT>(T_g[w]);
 }
 
+template <typename TT>
 __global__ void __launch_bounds__(128, 6) k_sweep_local(const __grid_constant__ Geom g,
                                                     const PhaseArgs a,
                                                     const __grid_constant__ Tables tab,
@@ -553,8 +560,9 @@ __global__ void __launch_bounds__(128, 6) k_sweep_local(const __grid_constant__ 
                                                     uint32_t n_active, uint32_t ax_n,
                                                     uint32_t ay_n, const LocalSplit split) {
   extern __shared__ __align__(16) unsigned char smem[];
-  load_local(smem, lp_g, T_g, n_T);
-  uint32_t* s_tab = reinterpret_cast<uint32_t*>(smem + kLocalParamBytes + 8 * n_T);
+  load_local<TT>(smem, lp_g, T_g, n_T);
+  uint32_t* s_tab = reinterpret_cast<uint32_t*>(smem + kLocalParamBytes +
+                                                (sizeof(TT) * n_T + 15) / 16 * 16);
   for (int w = threadIdx.x; w < kTabWords; w += blockDim.x) s_tab[w] = tab.w[w];
   const int n_items = lp_g->n_items;
   int* dv = reinterpret_cast<int*>(s_tab + kTabWords);
@@ -567,7 +575,7 @@ __global__ void __launch_bounds__(128, 6) k_sweep_local(const __grid_constant__ 
   const bool fast_ok = !g.pack4 && static_cast<int64_t>(g.nb) * g.n[2] * g.n[1] * g.px < (1ll << 31);
   __syncthreads();
   const LocalParam& lp = *reinterpret_cast<const LocalParam*>(smem);
-  const int64_t* T = reinterpret_cast<const int64_t*>(smem + kLocalParamBytes);
+  const TT* T = reinterpret_cast<const TT*>(smem + kLocalParamBytes);
   if (fast_ok) {
     for (int w = threadIdx.x; w < g.nb * lp.total; w += blockDim.x) {
       const int b = w / lp.total, t = w % lp.total;
@@ -661,10 +669,11 @@ __global__ void __launch_bounds__(128, 6) k_sweep_local(const __grid_constant__ 
                     nb_b += 1ull << (5 * sb);
                     nb_a += 1ull << (5 * sa);
                   }
-                  const int64_t* row_b = T + (static_cast<size_t>(m) * K + cb) * K * zt;
-                  const int64_t* row_a = T + (static_cast<size_t>(m) * K + ca) * K * zt;
+                  const TT* row_b = T + (static_cast<size_t>(m) * K + cb) * K * zt;
+                  const TT* row_a = T + (static_cast<size_t>(m) * K + ca) * K * zt;
                   for (int s = 0; s < K; ++s)
-                    de += row_a[s * zt + count_field(nb_a, s)] - row_b[s * zt + count_field(nb_b, s)];
+                    de += static_cast<int64_t>(row_a[s * zt + count_field(nb_a, s)]) -
+                          static_cast<int64_t>(row_b[s * zt + count_field(nb_b, s)]);
                 }
               };
               full(ai, b, p, q);
@@ -683,9 +692,9 @@ __global__ void __launch_bounds__(128, 6) k_sweep_local(const __grid_constant__ 
                   np += sn == cp;
                   nq += sn == cq;
                 }
-                const int64_t* row = T + (static_cast<size_t>(m) * K + c) * K * zt;
-                de += row[p * zt + np + dp] - row[p * zt + np] + row[q * zt + nq - dp] -
-                      row[q * zt + nq];
+                const TT* row = T + (static_cast<size_t>(m) * K + c) * K * zt;
+                de += static_cast<int64_t>(row[p * zt + np + dp]) - row[p * zt + np] +
+                      static_cast<int64_t>(row[q * zt + nq - dp]) - row[q * zt + nq];
               }
               bool accept;
               if (de <= 0 || a.mode == kModeAcceptAll) {
@@ -754,7 +763,7 @@ __global__ void __launch_bounds__(256) k_local_energy(const Geom g,
                                                       uint32_t n_cells) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ long long s_red[8];
-  load_local(smem, lp_g, T_g, n_T);
+  load_local<int64_t>(smem, lp_g, T_g, n_T);
   __syncthreads();
   const LocalParam& lp = *reinterpret_cast<const LocalParam*>(smem);
   const int64_t* T = reinterpret_cast<const int64_t*>(smem + kLocalParamBytes);
@@ -789,11 +798,13 @@ __global__ void __launch_bounds__(256) k_local_energy(const Geom g,
   }
 }
 
-size_t local_smem_bytes(int n_T) { return kLocalParamBytes + 8 * static_cast<size_t>(n_T); }
+size_t local_smem_bytes(int n_T, size_t entry = 8) {
+  return kLocalParamBytes + (entry * static_cast<size_t>(n_T) + 15) / 16 * 16;
+}
 
 cudaError_t launch_sweep_local(const Geom& g, const PhaseArgs& a, const Tables& tab,
                                uint8_t* occ, const LocalParam* lp, const int64_t* T, int n_T,
-                               int n_items, unsigned long long* stats, cudaStream_t st) {
+                               bool t32, int n_items, unsigned long long* stats, cudaStream_t st) {
   uint32_t cnt[2];
   for (int d = 0; d < 2; ++d) {
     if (g.m[d] == 1 && ((a.colour >> d) & 1)) return cudaSuccess;
@@ -801,8 +812,10 @@ cudaError_t launch_sweep_local(const Geom& g, const PhaseArgs& a, const Tables& 
   }
   if (a.naz <= 0) return cudaErrorInvalidValue;
   const uint32_t n_active = cnt[0] * cnt[1] * static_cast<uint32_t>(a.naz);
-  const size_t smem = local_smem_bytes(n_T) + 4 * kTabWords + local_fast_bytes(g.nb, g.z1, n_items);
-  cudaError_t e = cudaFuncSetAttribute(k_sweep_local, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  const size_t smem = local_smem_bytes(n_T, t32 ? 4 : 8) + 4 * kTabWords +
+                      local_fast_bytes(g.nb, g.z1, n_items);
+  auto kern = t32 ? k_sweep_local<int32_t> : k_sweep_local<int64_t>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        static_cast<int>(smem));
   if (e != cudaSuccess) return e;
   // interior cells first (a cell is interior when its sites and their reads,
@@ -837,8 +850,8 @@ cudaError_t launch_sweep_local(const Geom& g, const PhaseArgs& a, const Tables& 
     sp.s0[d] = s0;
     sp.I[d] = n_in;
   }
-  k_sweep_local<<<(n_active + 127) / 128, 128, smem, st>>>(g, a, tab, occ, lp, T, n_T, stats,
-                                                          n_active, cnt[0], cnt[1], sp);
+  kern<<<(n_active + 127) / 128, 128, smem, st>>>(g, a, tab, occ, lp, T, n_T, stats, n_active,
+                                                 cnt[0], cnt[1], sp);
   return cudaGetLastError();
 }
 

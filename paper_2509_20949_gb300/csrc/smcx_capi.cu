@@ -215,6 +215,7 @@ struct smcx_lattice {
   int zt = 0;                   // its table's count axis
   int n_T = 0;                  // its table's entries
   int n_items = 0;              // its bystander (site, shell) items per direction
+  bool t32 = false;             // every table entry fits int32
   int tiled_kmax = 0;
   // online kernel choice (SMCX_OPT_KERNEL = 0 and SMCX_OPT_TILE = -1): the
   // candidates (kernel, tile shape), the fastest phase seen for each, and
@@ -564,7 +565,7 @@ smcx_status launch_colour_with(smcx_lattice* lat, int colour, const PhaseArgs& b
     return fail(SMCX_EINVAL, "the requested kernel does not support this lattice/EPI/tile shape");
   if (kern == 4) {
     SMCX_CUDA(lat, launch_sweep_local(g, a, tab, lat->d_occ, lat->dlp(), lat->dT(), lat->n_T,
-                                      lat->n_items, lat->stats(), lat->stream));
+                                      lat->t32, lat->n_items, lat->stats(), lat->stream));
     return SMCX_OK;
   }
   if (kern == 3) {
@@ -865,6 +866,9 @@ smcx_status smcx_set_local_model(smcx_lattice* lat, uint32_t n_shells, const int
   lat->zt = static_cast<int>(zt);
   lat->n_T = static_cast<int>(n_T);
   lat->n_items = lp.n_items;
+  lat->t32 = true;
+  for (size_t i = 0; i < n_T; ++i)
+    lat->t32 = lat->t32 && t_q[i] >= INT32_MIN && t_q[i] <= INT32_MAX;
   lat->V.clear();
   lat->tiled_table_ok = false;
   lat->has_epi = true;

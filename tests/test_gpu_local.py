@@ -22,17 +22,19 @@ def _table(kind, M, K, seed, scale=0.02):
     return np.round(rng.normal(0.0, scale, (M, K, K, zt)) * 2.0 ** 32).astype(np.int64)
 
 
-@pytest.mark.parametrize("kind,n,K,M,pack", [
-    (0, (12, 9, 10), 4, 3, 8),   # BCC shells 1-3, ragged cells
-    (1, (8, 7, 9), 5, 3, 8),     # FCC shells 1-3
-    (0, (9, 12, 7), 3, 2, 4),    # 4-bit storage
-    (1, (6, 6, 13), 8, 1, 8),    # K = 8, one shell
-    (0, (4, 5, 4), 2, 3, 8),     # n_d = 4: the smallest lattice, one cell along x and z
+@pytest.mark.parametrize("kind,n,K,M,pack,scale", [
+    (0, (12, 9, 10), 4, 3, 8, 0.02),   # BCC shells 1-3, ragged cells
+    (1, (8, 7, 9), 5, 3, 8, 0.02),     # FCC shells 1-3
+    (0, (9, 12, 7), 3, 2, 4, 0.02),    # 4-bit storage
+    (1, (6, 6, 13), 8, 1, 8, 0.02),    # K = 8, one shell
+    (0, (4, 5, 4), 2, 3, 8, 0.02),     # n_d = 4: the smallest lattice, one cell along x and z
+    (0, (14, 13, 12), 4, 3, 8, 3.0),   # entries beyond int32: the int64 shared table
 ])
-def test_local_sweeps_match_the_oracle(orc, kind, n, K, M, pack):
+def test_local_sweeps_match_the_oracle(orc, kind, n, K, M, pack, scale):
     require_cuda()
     case = make_case(kind, n, K, M, seed=31, occ_seed=32)
-    T = _table(kind, M, K, seed=33)
+    T = _table(kind, M, K, seed=33, scale=scale)
+    assert (np.abs(T).max() > 2 ** 31) == (scale > 1.0)
     lat = gpu_lattice(case, pack_bits=pack)
     lat.set_local_model(T)
     assert lat.kernel_in_use()[0] == 4
