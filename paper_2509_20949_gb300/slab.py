@@ -100,6 +100,19 @@ class SlabSweep:
         buf = self.lat.planes_buffer(nz)
         return buf if self.device_comm else self._torch.empty_like(buf, device="cpu")
 
+    def _to_lattice(self, host_buf, nz):
+        """A received host buffer copied to a lattice buffer on the lattice's
+        own stream, so that the library calls that follow on that stream see
+        the copy complete."""
+        dev = self.lat.planes_buffer(nz)
+        stream = getattr(self.lat, "stream", None)
+        if stream is not None and dev.is_cuda:
+            with self._torch.cuda.stream(stream):
+                dev.copy_(host_buf)
+        else:
+            dev.copy_(host_buf)
+        return dev
+
     def _p2p(self, sends, recvs):
         """sends: [(peer, tensor, tag)], recvs: [(peer, tensor, tag)], posted
         as one batch (NCCL groups them, so no pair waits on the other's order)."""
@@ -109,6 +122,14 @@ class SlabSweep:
         if ops:
             for w in dist.batch_isend_irecv(ops):
                 w.wait()
+            self._after_comm()
+
+    def _after_comm(self):
+        """NCCL's completion orders PyTorch's current stream only: the lattice's
+        stream waits for it before the library reads received buffers."""
+        stream = getattr(self.lat, "stream", None)
+        if self.device_comm and stream is not None:
+            stream.wait_stream(self._torch.cuda.current_stream(self.lat.device))
 
     def _regions(self, p):
         h = p["halo"]
@@ -130,8 +151,8 @@ class SlabSweep:
         self._p2p([(up, self._wire(mine_hi), _TAG_UP), (down, self._wire(mine_lo), _TAG_DOWN)],
                   [(down, theirs_lo, _TAG_UP), (up, theirs_hi, _TAG_DOWN)])
         if not self.device_comm:
-            theirs_lo = lat.planes_buffer(nb).copy_(theirs_lo)
-            theirs_hi = lat.planes_buffer(nb).copy_(theirs_hi)
+            theirs_lo = self._to_lattice(theirs_lo, nb)
+            theirs_hi = self._to_lattice(theirs_hi, nb)
         lat.merge_planes(lo, nb, theirs_lo, before[0])
         lat.merge_planes(hi, nb, theirs_hi, before[1])
 
@@ -156,7 +177,7 @@ class SlabSweep:
         self._p2p([(p, self._wire(b), tag) for p, b, tag in sends], recvs)
         for z0, nz, buf in puts:
             if not self.device_comm:
-                buf = lat.planes_buffer(nz).copy_(buf)
+                buf = self._to_lattice(buf, nz)
             lat.put_planes(z0, nz, buf)
         lat.synchronize()
 
@@ -221,7 +242,8 @@ class SlabSweep:
             else:
                 buf = self._wire_empty(nz)
                 self._dist.broadcast(buf, src=self._global(src), group=self.group)
+                self._after_comm()
                 if not self.device_comm:
-                    buf = lat.planes_buffer(nz).copy_(buf)
+                    buf = self._to_lattice(buf, nz)
                 lat.put_planes(z0, nz, buf)
         lat.synchronize()
