@@ -87,6 +87,8 @@ SMALL = [
     (0, (12, 12, 12), 4, 3, 0, 3),     # min_cell raises the edge
     (1, (6, 6, 6), 1, 2, 0, 0),        # one species
     (0, (6, 6, 6), 12, 2, 0, 0),       # many species
+    (0, (1, 1, 1), 2, 1, 0, 0),        # the smallest lattice: two sites
+    (0, (6, 6, 6), 255, 2, 0, 0),      # the largest species count
 ]
 
 
