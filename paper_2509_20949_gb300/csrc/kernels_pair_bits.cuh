@@ -163,7 +163,12 @@ __global__ void __launch_bounds__(C::NT) k_pair_count_bits(const __grid_constant
       const int ty = r % bg.TY, t = r / bg.TY;
       const int tz = t % bg.TZ, b = t / bg.TZ;
       const int gy = pmod(y0 - C::H + ty, ny), gz = pmod(z0 - C::H + tz, nz);
-      const uint8_t* row = occ + ((static_cast<size_t>(b) * nz + gz) * ny + gy) * px;
+      // 8-bit storage: basis b's row holds codes sigma * W; 4-bit storage:
+      // row group b / 2 holds sigma of bases b & ~1 (low nibble) and b | 1
+      const int grp = g.pack4 ? b >> 1 : b;
+      const uint32_t sh = g.pack4 ? 4u * (b & 1) : 0u, fm = g.pack4 ? 0x0Fu : 0xFFu;
+      const uint32_t mul = g.pack4 ? 1u : static_cast<uint32_t>(C::W);
+      const uint8_t* row = occ + ((static_cast<size_t>(grp) * nz + gz) * ny + gy) * px;
       for (int s0 = 0; s0 < bg.NS; s0 += 8) {
         uint32_t wv[8];
 #pragma unroll
@@ -189,10 +194,10 @@ __global__ void __launch_bounds__(C::NT) k_pair_count_bits(const __grid_constant
           uint32_t bal[4][C::NQ];
 #pragma unroll
           for (int j = 0; j < 4; ++j) {
-            const uint32_t c = (wv[k] >> (8 * j)) & 0xFFu;
+            const uint32_t c = (wv[k] >> (8 * j + sh)) & fm;
 #pragma unroll
             for (int q = 0; q < C::NQ; ++q)
-              bal[j][q] = __ballot_sync(0xffffffffu, c == static_cast<uint32_t>(q * C::W));
+              bal[j][q] = __ballot_sync(0xffffffffu, c == static_cast<uint32_t>(q) * mul);
           }
           if (lane == 0) {  // the ballots are warp-uniform: one lane stores the chunks
             uint32_t* dst = s_mask + (r * bg.NS + s0 + k) * 4;
@@ -354,7 +359,7 @@ bool box_for(const Geom& g, size_t budget, BoxGeom* bg, size_t* smem) {
 
 template <class C>
 bool b_supported(const Geom& g) {
-  if (g.kind != C::KIND || g.pack4 || g.K > 6 || (g.K == 6) != (C::KMAX == 6)) return false;
+  if (g.kind != C::KIND || g.K > 6 || (g.K == 6) != (C::KMAX == 6)) return false;
   BoxGeom bg;
   size_t smem;
   return box_for<C>(g, 227 * 1024, &bg, &smem);

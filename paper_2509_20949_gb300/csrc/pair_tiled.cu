@@ -25,9 +25,9 @@ static cudaError_t pc_k(const Geom& g, const uint8_t* occ, unsigned long long* h
 
 // Half-shell counts H[m][p'][p] (m < n_shells, laid out with K_MAX = 5 or 6
 // species per row) into h (zeroed by the caller); the directed counts are
-// H + H^T.  8-bit lattices go to the bit-sliced kernel (pair_bits.cu), 4-bit
-// ones to the byte-tile kernel here.  cudaErrorNotSupported when the lattice
-// needs the generic kernel.
+// H + H^T.  The bit-sliced kernel (pair_bits.cu) takes 8- and 4-bit lattices
+// whose masks fit shared memory, the byte-tile kernel here the rest.
+// cudaErrorNotSupported when the lattice needs the generic kernel.
 cudaError_t launch_pair_count_tiled(const Geom& g, int n_shells, const uint8_t* occ,
                                     unsigned long long* h, int n_sm, cudaStream_t st,
                                     bool check_only) {

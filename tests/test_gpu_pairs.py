@@ -21,6 +21,10 @@ CASES = [
     (0, (31, 3, 2), 3, 3, 8),
     (1, (64, 12, 7), 2, 3, 8),
     (0, (64, 10, 10), 5, 3, 4),
+    (1, (130, 9, 11), 5, 4, 4),    # 4-bit storage: FCC, two row groups
+    (0, (129, 17, 10), 6, 4, 4),   # 4-bit, K = 6, ragged row length
+    (1, (33, 5, 3), 6, 2, 4),
+    (0, (31, 3, 2), 3, 3, 4),      # 4-bit, rows shorter than a span (wrap)
 ]
 
 
