@@ -612,10 +612,9 @@ def main():
             "trial_stats": trial_stats,
             "cpu_baseline": cpu,
             "clocks": clk,
-            # per step: 8 colour phases + the pair count (8-bit storage, K <= 6:
-            # bit-mask kernel + its one-thread finishing kernel)
-            "gpu_launches": args.steps * (launches_per_sweep +
-                                          (2 if args.pack_bits == 8 and w["K"] <= 6 else 1)),
+            # per step: 8 colour phases + the pair count (K <= 6: bit-mask
+            # kernel + its one-thread finishing kernel)
+            "gpu_launches": args.steps * (launches_per_sweep + (2 if w["K"] <= 6 else 1)),
         }
         print(json.dumps(line), flush=True)
     if world > 1:
