@@ -27,3 +27,14 @@ def test_recorded_profile_matches_kernel_source():
     # the committed ncu summary was taken on the current tiled-kernel source
     assert rec is not None and rec["dram_bytes_per_launch"] > 0
     assert 0 < rec["limiter"]["frac"] <= 1 and 0 < rec["limiter"]["issue_active_frac"] <= 1
+
+
+def test_local_model_cpu_baseline(orc):
+    """The --mode local line's CPU baseline: the oracle's local sweeps on a
+    bounded lattice of the workload's recipe."""
+    import bench
+    from paper_2509_20949_gb300 import inputs
+    w = inputs.workload("bcc812_k5")
+    cb = bench.cpu_baseline_local(w, 3, 1.0)
+    assert cb["kind"] == "oracle" and cb["cores"] == 1 and cb["value"] > 0
+    assert "lattice" in cb["sample"]
