@@ -67,6 +67,7 @@ def _run(case, world):
     (0, (6, 6, 16), 4, 2, 2),    # BCC, uniform cells
     (0, (6, 5, 13), 3, 3, 3),    # BCC, ragged z cells, three ranks
     (1, (4, 4, 12), 3, 4, 2),    # FCC, shells 1-4
+    (0, (5, 4, 17), 3, 2, 4),    # four ranks: distinct neighbours on both sides, ragged z cells
 ])
 def test_ranks_reproduce_the_single_lattice_sweeps(orc, kind, n, K, M, world):
     case = _case(kind, n, K, M, seed=40 + world)
