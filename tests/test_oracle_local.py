@@ -168,3 +168,24 @@ def test_synthetic_table_shape_and_zero_count(orc):
         assert np.all(T[..., 0] == 0)
         lin = T[..., 1:2] * np.arange(T.shape[3])[None, None, None, :]
         assert np.any(T != lin)
+
+
+def test_single_cell_boltzmann_fcc_nonlinear_table(orc):
+    """FCC 2x2x2 conventional cells, 4 minority atoms in 32 (35,960 states),
+    one sequential cell, shells 1-2 with a nonlinear table: the chain's
+    energy levels follow exp(-beta E) of the brute-force local energy."""
+    kind, n, M = 1, (2, 2, 2), 2
+    N = 32
+    T = _table(kind, M, 2, seed=19, scale=0.01)
+    states = np.array([[1 if i in c else 0 for i in range(N)]
+                       for c in itertools.combinations(range(N), 4)], dtype=np.uint8)
+    E = bf.local_energies(kind, n, T, states)
+    Temp = 1200.0
+    levels, p = _exact_levels(E, Temp)
+    d = orc.Desc(kind, n, 2, M, seed=8, flags=orc.FLAG_SINGLE_CELL)
+    occ = states[777].copy()
+    E0 = orc.local_energy(d, T, occ)
+    o, st = orc.local_sweeps(d, T, occ, 0, 20000, Temp)
+    Et = E0 + np.cumsum(st["sum_dE"].astype(np.int64))
+    assert Et[-1] == orc.local_energy(d, T, o)
+    _compare(levels, p, Et[500:])
