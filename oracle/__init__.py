@@ -20,6 +20,9 @@ Functions and the passages they follow:
   sweeps            full MC steps: one trial per site (Sec. 2.1) over the
                     checkerboard of link cells (Sec. 2.2)
   phase_cells       the trials of chosen cells of one colour phase
+  sweeps_par /      the same with the cells of one colour shared out over
+  phase_cells_par   OpenMP threads (cells of one colour never interact, so the
+                    results are the sequential ones bit for bit)
 """
 from __future__ import annotations
 
@@ -85,7 +88,11 @@ def build(force: bool = False) -> str:
     tmp = _LIB_PATH + f".tmp{os.getpid()}"
     cmd = ["gcc", "-O2", "-std=gnu11", "-fPIC", "-shared", "-ffp-contract=off",
            "-fno-fast-math", "-o", tmp, _SRC, "-lm"]
-    subprocess.run(cmd, check=True)
+    # the *_par functions share the cells of one colour out over OpenMP
+    # threads; without OpenMP they run on one thread (same results)
+    r = subprocess.run(cmd[:-4] + ["-fopenmp"] + cmd[-4:], capture_output=True, text=True)
+    if r.returncode != 0:
+        subprocess.run(cmd, check=True)
     os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
 
@@ -116,6 +123,16 @@ def _load():
                                             ctypes.c_uint32, ctypes.c_double, ctypes.c_int,
                                             P(ctypes.c_uint32), ctypes.c_uint32, P(_Stats)]
             lib.orc_sweep_shift.argtypes = [P(_Desc), ctypes.c_uint32, P(ctypes.c_int32)]
+            lib.orc_phase_cells_par.argtypes = [P(_Desc), P(ctypes.c_int64), P(ctypes.c_uint8),
+                                                ctypes.c_uint32, ctypes.c_double, ctypes.c_int,
+                                                P(ctypes.c_uint32), ctypes.c_uint32, ctypes.c_int,
+                                                P(_Stats)]
+            lib.orc_sweeps_par.argtypes = [P(_Desc), P(ctypes.c_int64), P(ctypes.c_uint8),
+                                           ctypes.c_uint32, ctypes.c_uint32, ctypes.c_double,
+                                           ctypes.c_double, P(_Stats), ctypes.c_int]
+            lib.orc_max_threads.argtypes = []
+            for name in ("orc_phase_cells_par", "orc_sweeps_par", "orc_max_threads"):
+                getattr(lib, name).restype = ctypes.c_int
             lib.orc_exchange.argtypes = [ctypes.c_uint32, P(ctypes.c_int64), P(ctypes.c_double),
                                          ctypes.c_uint64, ctypes.c_uint32, P(ctypes.c_uint32),
                                          P(ctypes.c_uint8)]
@@ -308,6 +325,47 @@ def phase_cells(desc: Desc, V, occ, t: int, T: float, colour: int, cids, inplace
                                _ptr(o, ctypes.c_uint8), int(t), float(T), int(colour),
                                _ptr(c, ctypes.c_uint32), len(c), ctypes.byref(st)), "phase_cells")
     return o, dict(attempts=st.attempts, unlike=st.unlike, accepted=st.accepted, sum_dE=st.sum_dE)
+
+
+def max_threads() -> int:
+    """Threads the *_par functions use by default (1 without OpenMP)."""
+    return int(_load().orc_max_threads())
+
+
+def phase_cells_par(desc: Desc, V, occ, t: int, T: float, colour: int, cids, n_threads=None,
+                    inplace=False):
+    """phase_cells with the cells shared out over n_threads OpenMP threads
+    (cells of one colour never interact: same occupancy and statistics)."""
+    lib = _load()
+    o = occ if inplace else np.array(occ, dtype=np.uint8, copy=True, order="C")
+    if inplace and (o.dtype != np.uint8 or not o.flags.c_contiguous):
+        raise OracleError("in-place replay needs a contiguous uint8 array")
+    v = _V(V)
+    c = np.ascontiguousarray(cids, dtype=np.uint32)
+    st = _Stats()
+    nt = max_threads() if n_threads is None else int(n_threads)
+    _check(lib.orc_phase_cells_par(ctypes.byref(desc.c()), _ptr(v, ctypes.c_int64),
+                                   _ptr(o, ctypes.c_uint8), int(t), float(T), int(colour),
+                                   _ptr(c, ctypes.c_uint32), len(c), nt, ctypes.byref(st)),
+           "phase_cells_par")
+    return o, dict(attempts=st.attempts, unlike=st.unlike, accepted=st.accepted, sum_dE=st.sum_dE)
+
+
+def sweeps_par(desc: Desc, V, occ, t0: int, n_sweeps: int, T_first: float, T_last=None,
+               n_threads=None):
+    """sweeps with the cells of each colour shared out over n_threads OpenMP
+    threads (same occupancy and per-sweep statistics)."""
+    lib = _load()
+    o = np.array(occ, dtype=np.uint8, copy=True, order="C")
+    v = _V(V)
+    stats = np.zeros(n_sweeps, dtype=STATS_DTYPE)
+    T_last = T_first if T_last is None else T_last
+    nt = max_threads() if n_threads is None else int(n_threads)
+    code = lib.orc_sweeps_par(ctypes.byref(desc.c()), _ptr(v, ctypes.c_int64),
+                              _ptr(o, ctypes.c_uint8), int(t0), int(n_sweeps), float(T_first),
+                              float(T_last), stats.ctypes.data_as(ctypes.POINTER(_Stats)), nt)
+    _check(code, "sweeps_par")
+    return o, stats
 
 
 def sweep_shift(desc: Desc, t: int):

@@ -28,7 +28,8 @@
  * from coordinates, every energy change is the literal sum with every
  * occurrence of the two swapped sites left out.
  *
- * Build: gcc -O2 -std=c11 -fPIC -shared -ffp-contract=off (no fast-math).
+ * Build: gcc -O2 -std=c11 -fPIC -shared -ffp-contract=off (no fast-math), with
+ * -fopenmp where the compiler has it (only the *_par functions use it).
  */
 #include <math.h>
 #include <stdint.h>
@@ -675,6 +676,131 @@ int orc_phase_cells(const orc_desc *d, const int64_t *V, uint8_t *occ, uint32_t 
     run_cell(&cx, cid, &st);
   }
   if (st_out) *st_out = st;
+  return ORC_OK;
+}
+
+/* ------------------------------------------------------------------------ */
+/* The same trials with the cells of one colour shared out over OpenMP      */
+/* threads (the CPU baseline on all host cores, and whole-phase replays of  */
+/* lattices too large for one core).  Cells of one colour never touch one   */
+/* another's interaction zones (the link-cell edge rule of Sec. 2.2), so    */
+/* each cell's trials read and write the same values whatever the order or  */
+/* thread: the occupancy is that of the sequential functions above, bit for */
+/* bit, and the integer statistics are per-thread sums added at the end     */
+/* (order-free).  Built without OpenMP these run on one thread.             */
+/* ------------------------------------------------------------------------ */
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+int orc_max_threads(void) {
+#ifdef _OPENMP
+  return omp_get_max_threads();
+#else
+  return 1;
+#endif
+}
+
+static void run_cells_par(sweep_ctx *cx, const uint32_t *cids, uint32_t n, int n_threads,
+                          orc_stats *st) {
+  uint64_t att = 0, unl = 0, acc = 0;
+  int64_t sde = 0;
+  if (n_threads < 1) n_threads = 1;
+#ifdef _OPENMP
+#pragma omp parallel for schedule(dynamic, 64) num_threads(n_threads) \
+    reduction(+ : att, unl, acc, sde)
+#endif
+  for (int64_t a = 0; a < (int64_t)n; ++a) {
+    orc_stats one = {0, 0, 0, 0};
+    run_cell(cx, cids[a], &one);
+    att += one.attempts;
+    unl += one.unlike;
+    acc += one.accepted;
+    sde += one.sum_dE;
+  }
+  st->attempts += att;
+  st->unlike += unl;
+  st->accepted += acc;
+  st->sum_dE += sde;
+}
+
+int orc_phase_cells_par(const orc_desc *d, const int64_t *V, uint8_t *occ, uint32_t t, double T,
+                        int colour, const uint32_t *cids, uint32_t n, int n_threads,
+                        orc_stats *st_out) {
+  if (!valid_desc(d)) return ORC_EINVAL;
+  shells_t sh;
+  build_shells(d->kind, d->M, &sh);
+  sweep_ctx cx;
+  cx.d = d;
+  cx.sh = &sh;
+  cx.V = V;
+  cx.T = NULL;
+  cx.zt = 0;
+  cx.occ = occ;
+  compute_layout(d, &sh, 0, &cx.lay, 0);
+  uint32_t tab[3 * 512];
+  int code = orc_thresholds(T, tab, &cx.s, &cx.mode);
+  if (code != ORC_OK) return code;
+  cx.tab = tab;
+  cx.t = t;
+  sweep_shift(d, t, cx.shift);
+  uint32_t n_cells = (uint32_t)cx.lay.m[0] * cx.lay.m[1] * cx.lay.m[2];
+  for (uint32_t a = 0; a < n; ++a) {
+    uint32_t cid = cids[a];
+    if (cid >= n_cells) return ORC_EINVAL;
+    int cxi = (int)(cid % (uint32_t)cx.lay.m[0]);
+    int cyi = (int)((cid / (uint32_t)cx.lay.m[0]) % (uint32_t)cx.lay.m[1]);
+    int czi = (int)(cid / ((uint32_t)cx.lay.m[0] * (uint32_t)cx.lay.m[1]));
+    if (cell_colour(&cx.lay, cxi, cyi, czi) != colour) return ORC_EINVAL;
+  }
+  orc_stats st = {0, 0, 0, 0};
+  run_cells_par(&cx, cids, n, n_threads, &st);
+  if (st_out) *st_out = st;
+  return ORC_OK;
+}
+
+int orc_sweeps_par(const orc_desc *d, const int64_t *V, uint8_t *occ, uint32_t t0,
+                   uint32_t n_sweeps, double T_first, double T_last, orc_stats *per_sweep,
+                   int n_threads) {
+  if (!valid_desc(d) || !validate_occ(d, occ)) return ORC_EINVAL;
+  shells_t sh;
+  build_shells(d->kind, d->M, &sh);
+  sweep_ctx cx;
+  cx.d = d;
+  cx.sh = &sh;
+  cx.V = V;
+  cx.T = NULL;
+  cx.zt = 0;
+  cx.occ = occ;
+  compute_layout(d, &sh, 0, &cx.lay, 0);
+  uint32_t n_cells = (uint32_t)cx.lay.m[0] * cx.lay.m[1] * cx.lay.m[2];
+  uint32_t *order = (uint32_t *)malloc(sizeof(uint32_t) * n_cells);
+  if (!order) return ORC_EINVAL;
+  uint32_t tab[3 * 512];
+  for (uint32_t sw = 0; sw < n_sweeps; ++sw) {
+    double T = sweep_temperature(T_first, T_last, sw, n_sweeps);
+    int st_code = orc_thresholds(T, tab, &cx.s, &cx.mode);
+    if (st_code != ORC_OK) {
+      free(order);
+      return st_code;
+    }
+    cx.tab = tab;
+    cx.t = t0 + sw;
+    sweep_shift(d, cx.t, cx.shift);
+    orc_stats st = {0, 0, 0, 0};
+    for (int colour = 0; colour < 8; ++colour) {
+      uint32_t n_sel = 0;
+      for (uint32_t cid = 0; cid < n_cells; ++cid) {
+        int cxi = (int)(cid % (uint32_t)cx.lay.m[0]);
+        int cyi = (int)((cid / (uint32_t)cx.lay.m[0]) % (uint32_t)cx.lay.m[1]);
+        int czi = (int)(cid / ((uint32_t)cx.lay.m[0] * (uint32_t)cx.lay.m[1]));
+        if (cell_colour(&cx.lay, cxi, cyi, czi) == colour) order[n_sel++] = cid;
+      }
+      run_cells_par(&cx, order, n_sel, n_threads, &st);
+    }
+    if (per_sweep) per_sweep[sw] = st;
+  }
+  free(order);
   return ORC_OK;
 }
 
