@@ -36,7 +36,8 @@ if ROOT not in sys.path:
 
 from paper_2509_20949_gb300 import inputs  # noqa: E402
 
-METRIC = "attempted MC swaps/sec on 1 GB300 (plain single-lattice sweep)"
+METRIC = ("attempted MC swaps/sec on 1 GB300 (plain single-lattice sweep; batched and served "
+          "forms in the line's batched/served objects)")
 UNIT = "swaps/s"
 
 
@@ -62,6 +63,12 @@ def parse():
     ap.add_argument("--rate", type=float, default=5.0)
     ap.add_argument("--window", type=float, default=10.0)
     ap.add_argument("--budget-gb", type=float, default=160.0)
+    ap.add_argument("--no-batched", action="store_true",
+                    help="plain mode: leave out the batched (256-job) measurement")
+    ap.add_argument("--no-served", action="store_true",
+                    help="plain mode: leave out the served (Poisson trace) measurement")
+    ap.add_argument("--served-rate", type=float, default=1.0)
+    ap.add_argument("--served-window", type=float, default=10.0)
     return ap.parse_args()
 
 
@@ -171,30 +178,55 @@ def dist_setup():
     return world, rank, local
 
 
+def host_cpu():
+    """Host CPU of this machine: logical CPUs and model name (lscpu)."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name:"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except Exception:
+        pass
+    return {"nproc": os.cpu_count(), "model": model}
+
+
+def _oracle_rate(oracle, d, V, scratch, T, cids, seconds, threads):
+    """Trials/s of the oracle replaying the listed cells of colour 0 of sweep
+    0 in place, on `threads` threads, over about `seconds` of work."""
+    n_cal = min(len(cids), 256 * max(1, threads))
+    t0 = time.perf_counter()
+    oracle.phase_cells_par(d, V, scratch, 0, T, 0, cids[:n_cal], n_threads=threads, inplace=True)
+    per_cell = max((time.perf_counter() - t0) / n_cal, 1e-8)
+    n = int(min(len(cids) - n_cal, max(64, seconds / per_cell)))
+    sel = cids[n_cal:n_cal + n]
+    t0 = time.perf_counter()
+    _, st = oracle.phase_cells_par(d, V, scratch, 0, T, 0, sel, n_threads=threads, inplace=True)
+    dt = time.perf_counter() - t0
+    return int(st["attempts"]) / dt, len(sel), int(st["attempts"]), dt
+
+
 def cpu_baseline(w, N, V, occ, seconds, rank):
-    """The oracle as it stands, single-threaded on the host, replaying the
-    trials of a bounded sample of link cells of colour 0 of sweep 0 on the
-    full lattice."""
+    """The oracle as it stands on the host: its OpenMP variant (the cells of
+    one colour shared out over every host core; same results as the
+    sequential oracle) replaying a bounded sample of link cells of colour 0
+    of sweep 0 on the full lattice, and the sequential rate on one core."""
     import oracle
 
     d = oracle.Desc(w["kind"], w["n"], w["K"], w["M"], seed=w["seed"])
     cids = _colour_cells(oracle, d, 0)
     scratch = np.array(occ, copy=True)
     T = sweep_temperature(w, 0)
-    # calibrate on a small sample, then run ~`seconds` of work
-    n_cal = 256
-    t0 = time.perf_counter()
-    _, st = oracle.phase_cells(d, V, scratch, 0, T, 0, cids[:n_cal], inplace=True)
-    dt = time.perf_counter() - t0
-    per_cell = max(dt / n_cal, 1e-7)
-    n = int(min(len(cids) - n_cal, max(64, seconds / per_cell)))
-    t0 = time.perf_counter()
-    _, st = oracle.phase_cells(d, V, scratch, 0, T, 0, cids[n_cal:n_cal + n], inplace=True)
-    dt = time.perf_counter() - t0
-    att = int(st["attempts"])
-    return {"value": att / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"{n} link cells ({att} trials) of colour 0, sweep 0 of the full lattice, "
-                      f"{dt:.1f} s single-threaded"}
+    threads = oracle.max_threads()
+    half = len(cids) // 2
+    v1, n1, a1, t1 = _oracle_rate(oracle, d, V, scratch, T, cids[:half], seconds / 3, 1)
+    vp, n_p, ap, tp = _oracle_rate(oracle, d, V, scratch, T, cids[half:], seconds * 2 / 3, threads)
+    return {"value": vp, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "single_core_value": v1, "host": host_cpu(),
+            "sample": f"{n_p} link cells ({ap} trials) of colour 0, sweep 0 of the full lattice, "
+                      f"{tp:.1f} s on {threads} threads (cells of one colour in parallel); "
+                      f"one core: {n1} cells, {a1} trials, {t1:.1f} s"}
 
 
 def _colour_cells(oracle, d, colour):
@@ -220,7 +252,9 @@ def run_reference(args):
     oracle.build()
     d = oracle.Desc(w["kind"], w["n"], w["K"], w["M"], seed=w["seed"])
     cids = _colour_cells(oracle, d, 0)
-    per_step = min(len(cids), max(64, min(32768, len(cids) // max(1, args.steps + args.warmup))))
+    threads = oracle.max_threads()
+    per_step = min(len(cids), max(64, min(32768 * threads,
+                                          len(cids) // max(1, args.steps + args.warmup))))
     scratch = np.array(occ, copy=True)
     pos = 0
     times, atts = [], []
@@ -230,7 +264,8 @@ def run_reference(args):
         sel = cids[pos:pos + per_step]
         pos += per_step
         t0 = time.perf_counter()
-        _, st = oracle.phase_cells(d, V, scratch, 0, sweep_temperature(w, 0), 0, sel, inplace=True)
+        _, st = oracle.phase_cells_par(d, V, scratch, 0, sweep_temperature(w, 0), 0, sel,
+                                       n_threads=threads, inplace=True)
         dt = time.perf_counter() - t0
         if s >= args.warmup:
             times.append(dt)
@@ -241,9 +276,11 @@ def run_reference(args):
             "ms_per_step": 1e3 * sum(times) / len(times), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
             "config": {"workload": desc, "sample_per_step": f"{per_step} link cells of colour 0"},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                             "host": host_cpu(),
                              "sample": f"{per_step} link cells per step of colour 0, sweep 0, "
-                                       "full lattice in host memory"},
+                                       f"full lattice in host memory, {threads} threads "
+                                       "(cells of one colour in parallel)"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -403,6 +440,146 @@ def run_slab(args):
     return 0
 
 
+def measure_batched(n_jobs=256, chunk=50, sample_stride=8):
+    """C4, the 256-job mix (n ~ log-U(8, 64) conventional cells, BCC/FCC,
+    K ~ U{3..6}, shells 1-3, T ~ U(300, 1500) K, 200 sweeps each): all jobs
+    batched (graph-captured chunks of sweeps over every job) against the same
+    jobs one at a time through smcx_sweep, on a 1-in-`sample_stride` sample
+    of the jobs (each job's sweeps timed alone, lattices already on the
+    device).  Every sampled job ends in the same bits both ways."""
+    import torch
+
+    from paper_2509_20949_gb300.batch import Batch
+    from paper_2509_20949_gb300.lattice import Lattice
+
+    jobs = inputs.batch_jobs(n_jobs)
+    arrays = [_job_arrays(j) for j in jobs]
+    attempts = sum(inputs.n_sites(j["kind"], j["n"]) * j["sweeps"] for j in jobs)
+    heap = sum(Batch.job_bytes(j["kind"], j["n"], j["K"]) for j in jobs)
+    transfer = max(inputs.n_sites(j["kind"], j["n"]) for j in jobs)
+    b = Batch(len(jobs), Batch.control_bytes(len(jobs), transfer) + heap + (1 << 20), transfer)
+    ids = [b.add(j["kind"], j["n"], j["K"], occ, V, j["T_first"], j["sweeps"], seed=j["seed"])
+           for j, (V, occ) in zip(jobs, arrays)]
+    torch.cuda.synchronize()
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    t0 = time.perf_counter()
+    done = 0
+    while done < len(ids):
+        b.run(chunk)
+        done += len(b.poll())
+    torch.cuda.synchronize()
+    t_batch = time.perf_counter() - t0
+    clk = clocks.stop()
+    pick = list(range(0, len(jobs), sample_stride))
+    t_single, att_single, same = 0.0, 0, True
+    for k in pick:
+        j, (V, occ) = jobs[k], arrays[k]
+        lat = Lattice(j["kind"], j["n"], j["K"], occ, seed=j["seed"])
+        lat.set_epi(V)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        lat.sweep(j["sweeps"], j["T_first"], stats=False)
+        torch.cuda.synchronize()
+        t_single += time.perf_counter() - t0
+        att_single += inputs.n_sites(j["kind"], j["n"]) * j["sweeps"]
+        r = b.result(ids[k])
+        same = same and np.array_equal(r["occ"], lat.occupancy()) and \
+            r["energy"] == lat.running_energy() == lat.energy()
+        lat.close()
+    b.close()
+    one = att_single / t_single
+    return {"value": attempts / t_batch, "unit": UNIT, "one_at_a_time": one,
+            "speedup": (attempts / t_batch) / one, "identical_results": bool(same),
+            "jobs": len(jobs), "trials": attempts, "seconds": t_batch,
+            "one_at_a_time_sample": f"{len(pick)} of {len(jobs)} jobs (every {sample_stride}th), "
+                                    f"{att_single} trials in {t_single:.2f} s",
+            "config": f"{len(jobs)} jobs, {sum(inputs.n_sites(j['kind'], j['n']) for j in jobs)} "
+                      f"sites, 200 sweeps each, chunk {chunk} sweeps", "clocks": clk}
+
+
+def fifo_one_at_a_time(trace, deadline_s, chunk=50):
+    """Baseline of the served trace: one job at a time in arrival order
+    (FIFO), each uploaded as its own lattice when it starts and swept
+    through smcx_sweep in chunks of `chunk` sweeps (so the deadline can stop
+    it); latency = arrival -> result on the host."""
+    import torch
+
+    from paper_2509_20949_gb300.lattice import Lattice
+
+    t0 = time.perf_counter()
+    lat_s, swaps, results = [], 0, {}
+    for j in sorted(trace, key=lambda j: j["arrival_s"]):
+        while time.perf_counter() - t0 < j["arrival_s"]:
+            time.sleep(min(0.01, j["arrival_s"] - (time.perf_counter() - t0)))
+        if time.perf_counter() - t0 > deadline_s:
+            break
+        lat = Lattice(j["kind"], j["n"], j["K"], j["occ"], seed=j["seed"])
+        lat.set_epi(j["V"])
+        sites = inputs.n_sites(j["kind"], j["n"])
+        done = 0
+        while done < j["sweeps"] and time.perf_counter() - t0 <= deadline_s:
+            k = min(chunk, j["sweeps"] - done)
+            lat.sweep(k, j["T"], stats=False)
+            torch.cuda.synchronize()
+            done += k
+            swaps += sites * k
+        if done == j["sweeps"]:
+            results[j["job"]] = lat.occupancy()
+            lat_s.append(time.perf_counter() - t0 - j["arrival_s"])
+        lat.close()
+    elapsed = time.perf_counter() - t0
+    lat_a = np.array(lat_s)
+    return {"swaps_per_s": swaps / elapsed, "completed": len(lat_s),
+            "p50_latency_s": float(np.percentile(lat_a, 50)) if len(lat_a) else None,
+            "p99_latency_s": float(np.percentile(lat_a, 99)) if len(lat_a) else None,
+            "elapsed_s": elapsed}, results
+
+
+def measure_served(rate=1.0, window=10.0, budget_gb=160.0, chunk=50, deadline=None, seed=11):
+    """C5 at one arrival rate: Poisson arrivals over `window` s of lattices
+    with 1e4-1e8 sites and 100-5000 sweeps (log-uniform), composition or
+    temperature scans, admitted by the HBM budget into the continuous-
+    batching server (state resident between chunks); then the same trace
+    FIFO one job at a time.  p50/p99 latency of the completed jobs,
+    aggregate swaps/s of all swaps run, and whether every job completed both
+    ways ended in the same bits."""
+    import torch
+
+    from paper_2509_20949_gb300.server import Server
+
+    deadline = 3.0 * window if deadline is None else deadline
+    trace = inputs.served_jobs(rate, window, seed=seed)
+    for j in trace:
+        j["V"], j["occ"] = _job_arrays(j)
+    offered = sum(inputs.n_sites(j["kind"], j["n"]) * j["sweeps"] for j in trace)
+    srv = Server(int(budget_gb * (1 << 30)), max_jobs=1024, chunk_sweeps=chunk,
+                 transfer_bytes=(1 << 27))
+    torch.cuda.synchronize()
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    m = srv.run_trace(trace, deadline_s=deadline)
+    clk = clocks.stop()
+    served_occ = {srv.done[t]["job"]: srv.done[t]["occ"] for t in srv.done
+                  if "job" in srv.done[t]}
+    srv.close()
+    del srv
+    torch.cuda.empty_cache()
+    fifo, fifo_occ = fifo_one_at_a_time(trace, deadline, chunk)
+    both = [k for k in fifo_occ if k in served_occ]
+    same = all(np.array_equal(served_occ[k], fifo_occ[k]) for k in both)
+    return {"value": m["swaps_per_s"], "unit": UNIT,
+            "p50_latency_s": m["p50_latency_s"], "p99_latency_s": m["p99_latency_s"],
+            "completed": m["completed"], "submitted": m["submitted"],
+            "finished_jobs_swaps_per_s": m["finished_swaps_per_s"],
+            "offered_trials": offered, "elapsed_s": m["elapsed_s"],
+            "fifo_one_at_a_time": fifo,
+            "identical_results": {"jobs_compared": len(both), "same": bool(same)},
+            "config": f"Poisson {rate}/s over {window} s ({len(trace)} jobs), sites "
+                      f"log-U(1e4,1e8), sweeps log-U(100,5000), budget {budget_gb} GB, chunk "
+                      f"{chunk} sweeps, deadline {deadline} s", "clocks": clk}
+
+
 def run_batch(args):
     """256 independent lattices (n ~ log-U(8, 64) conventional cells, BCC/FCC,
     K ~ U{3..6}, shells 1-3, T ~ U(300, 1500) K, 200 sweeps each): batched
@@ -542,8 +719,8 @@ def main():
     time.sleep(0.3)
     ev_sweep = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
                 for _ in range(args.steps)]
-    ev0 = torch.cuda.Event(enable_timing=True)
-    ev1 = torch.cuda.Event(enable_timing=True)
+    ev_step = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+    ev0 = ev_step[0]
     ev0.record(stream)
     for s in range(args.steps):
         a, b = ev_sweep[s]
@@ -551,11 +728,13 @@ def main():
         step(args.warmup + s)
         b.record(stream)
         lat.sro(M)  # pair counts -> host (the step's result)
-    ev1.record(stream)
+        ev_step[s + 1].record(stream)
+    ev1 = ev_step[-1]
     torch.cuda.synchronize()
     clk = clocks.stop()
     t_ms = ev0.elapsed_time(ev1)
     sweep_ms = sum(a.elapsed_time(b) for a, b in ev_sweep)
+    step_ms = [ev_step[s].elapsed_time(ev_step[s + 1]) for s in range(args.steps)]
     t_ms = max_over_ranks(t_ms)
     total_attempts = N * args.steps * world
     value = total_attempts / (t_ms / 1e3)
@@ -593,6 +772,16 @@ def main():
     trial_stats = {"unlike_frac": ts["unlike"] / ts["attempts"],
                    "accepted_frac": ts["accepted"] / ts["attempts"],
                    "accepted_per_unlike": ts["accepted"] / max(1, ts["unlike"])}
+    batched = served = None
+    if world == 1 and (not args.no_batched or not args.no_served):
+        lat.close()
+        del lat
+        torch.cuda.empty_cache()
+        if not args.no_batched:
+            batched = measure_batched(args.jobs, args.chunk)
+        if not args.no_served:
+            served = measure_served(args.served_rate, args.served_window, args.budget_gb,
+                                    args.chunk)
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -608,8 +797,13 @@ def main():
                          "kernel": "sweep phase", "kernel_ms_per_launch": kernel_ms,
                          "peak_source": peak_src,
                          "limiter": rec.get("limiter") if rec else None},
+            "step_ms": {"median": statistics.median(step_ms), "min": min(step_ms),
+                        "max": max(step_ms), "repeats": len(step_ms)},
+            "value_median": N * world / (statistics.median(step_ms) / 1e3),
             "kernel_choice": kernel_choice,
             "trial_stats": trial_stats,
+            "batched": batched,
+            "served": served,
             "cpu_baseline": cpu,
             "clocks": clk,
             # per step: 8 colour phases + the pair count (K <= 6: bit-mask

@@ -102,8 +102,10 @@ smcx_status smcx_create_lattice(const smcx_lattice_desc* desc, void* d_occ, void
    in q units, symmetric in the species indices; n_shells in 1..4.  The link
    cells are sized from the shells (edge L = floor((1 + h_R)/2) + 1
    conventional cells, h_R the largest |component| of a shell vector, raised
-   to min_cell).  Restarts the running energy (see smcx_running_energy).
-   EINVAL: n_shells out of range, asymmetric V or a value beyond 2^52 q. */
+   to min_cell).  Restarts the running energy (see smcx_running_energy),
+   which runs one pair count.  EINVAL: n_shells out of range, asymmetric V
+   or a value beyond 2^52 q.  EOVERFLOW: the energy of the current
+   configuration does not fit int64. */
 smcx_status smcx_set_epi(smcx_lattice* lat, uint32_t n_shells, const int64_t* v_q);
 
 /* Runs n_sweeps MC steps (one trial per site each, Sec. 2.1) on the stream.
@@ -129,12 +131,13 @@ smcx_status smcx_run_colour(smcx_lattice* lat, uint32_t colour, double T, smcx_s
    fit int64.  ESTATE: no EPI. */
 smcx_status smcx_energy(smcx_lattice* lat, int64_t* e_q);
 
-/* Running energy: the energy at the last restart (smcx_set_epi,
-   smcx_set_occupancy, smcx_restore) plus the exact sum of every accepted
-   energy change since.  The base is computed on the first call after a
-   restart, as the full energy at that time minus the accepted changes so far
-   (equal by the incremental identity); later calls only read the device sum.
-   Synchronises.  EOVERFLOW: the full energy does not fit int64. */
+/* Running energy: E_0 + the exact sum of every energy change accepted since
+   the last restart.  E_0 is the full energy (a pair count) taken AT the
+   restart -- smcx_set_epi, smcx_set_local_model, smcx_set_occupancy -- or
+   the running energy stored in the checkpoint by smcx_restore, so comparing
+   it with smcx_energy later checks the incremental bookkeeping against a
+   recompute.  Only reads the device sum.  Synchronises.  ESTATE: no model
+   set. */
 smcx_status smcx_running_energy(smcx_lattice* lat, int64_t* e_q);
 
 /* Warren-Cowley SRO, Sec. 3.2, Eq. 9.  pair_counts (host, required) receives
@@ -151,7 +154,8 @@ smcx_status smcx_get_occupancy(smcx_lattice* lat, uint8_t* h_out);
 
 /* Replaces the occupancy by h_in (N bytes, canonical, ids < K, validated on
    the device; on EINVAL the occupancy is left as it was) and restarts the
-   running energy.  The sweep counter is unchanged.  Synchronises. */
+   running energy (one pair count once a model is set).  The sweep counter
+   is unchanged.  Synchronises. */
 smcx_status smcx_set_occupancy(smcx_lattice* lat, const uint8_t* h_in);
 
 /* Composition profile along a cylinder (the atom-probe-like analysis of
@@ -499,9 +503,11 @@ smcx_status smcx_batch_destroy(smcx_batch* b);
    no handle and no workspace and never allocates: its accumulators live in
    a static device array of the library holding SMCX_NOALLOC_MAX_SHELLS x
    SMCX_NOALLOC_MAX_SPECIES^2 counters (8 KiB), which every GPU that loads
-   the library keeps until the process exits.  The first call on a device
-   looks up that array's device address (cudaGetSymbolAddress) with the
-   device current; make it before any stream capture.  All calls on a device
+   the library keeps until the process exits.  Every call looks up that
+   array's device address for the current device and context
+   (cudaGetSymbolAddress, a host-side query; a kept address could outlive a
+   cudaDeviceReset).  The first call on a device also loads the library's
+   module there, so make it before any stream capture.  All calls on a device
    share the array, which is cleared at the start of each call and keeps the
    last call's counts afterwards: calls whose work overlaps on the GPU (other
    streams, other threads) race and must be serialised by the caller.  Pairs

@@ -12,9 +12,7 @@
 // the library holds until the process exits.  It is a variant of the
 // generic pair-count kernel: same counting, canonical site indexing, the
 // static array as its scratch.
-#include <mutex>
 #include <string>
-#include <vector>
 
 #include "../../include/smcx.h"
 #include "smcx_common.cuh"
@@ -33,9 +31,6 @@ constexpr int kScratchCounters = kMaxShellsNA * kMaxSpeciesNA * kMaxSpeciesNA;
 
 // the scratch: shared by every call on a device (see smcx.h)
 static __device__ __align__(256) unsigned long long g_na_scratch[kScratchCounters];
-
-std::mutex g_na_mutex;
-std::vector<void*> g_na_addr;  // device address of g_na_scratch per device, set up once
 
 struct NaGeom {
   int kind, nb;
@@ -99,24 +94,20 @@ __global__ void k_na_copy(const unsigned long long* __restrict__ scratch,
     out[i] = scratch[i];
 }
 
-// device address of the scratch on the current device (looked up once per
-// device, with that device current)
+// Device address of the scratch in the current device's current context.
+// In host code g_na_scratch names a host-side stand-in, not device memory, so
+// the address is asked of the runtime -- on every call, with the caller's
+// device current: a symbol's address belongs to one context, and an address
+// kept from an earlier call could point into a context that cudaDeviceReset
+// (or a switch of context) has since destroyed.  The query is a host-side
+// lookup; the first one on a device loads the library's module there.
 smcx_status na_scratch_address(void** out) {
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess)
-    return smcx::batch_fail(SMCX_ECUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
-  std::lock_guard<std::mutex> lock(g_na_mutex);
-  if (static_cast<int>(g_na_addr.size()) <= dev) g_na_addr.resize(dev + 1, nullptr);
-  if (!g_na_addr[dev]) {
-    void* p = nullptr;
-    e = cudaGetSymbolAddress(&p, g_na_scratch);
-    if (e != cudaSuccess || !p)
-      return smcx::batch_fail(SMCX_ECUDA,
-                              std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
-    g_na_addr[dev] = p;
-  }
-  *out = g_na_addr[dev];
+  void* p = nullptr;
+  const cudaError_t e = cudaGetSymbolAddress(&p, g_na_scratch);
+  if (e != cudaSuccess || !p)
+    return smcx::batch_fail(SMCX_ECUDA,
+                            std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
+  *out = p;
   return SMCX_OK;
 }
 

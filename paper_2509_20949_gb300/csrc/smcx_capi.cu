@@ -205,7 +205,7 @@ struct smcx_lattice {
   int m[3] = {1, 1, 1};
   uint32_t t = 0;
   int64_t E0 = 0;         // energy when the running energy was last restarted
-  bool e0_known = false;  // E0 is found on first request: E(now) - sum of accepted dE since
+  bool e0_known = false;  // E0 was taken (at the last restart with a model, or a restore)
   smcx_status sticky = SMCX_OK;
   int opt_kernel = 0;
   int opt_tile = -1;
@@ -465,13 +465,20 @@ smcx_status full_energy(smcx_lattice* lat, int64_t* e) {
   return energy_from_counts(lat, cnt, e);
 }
 
-// Restarts the running energy: the accepted-dE sums start again from zero.
-// Its base E0 (the energy now) is computed when first asked for, as the full
-// energy at that time minus the exact int64 sum of the dE accepted since:
-// no pair count on every occupancy upload.
+// Restarts the running energy: the accepted-dE sums start again from zero
+// and its base E0 is the full energy of the configuration now (one pair
+// count, or the local-energy reduction), so that E0 + the sum of accepted dE
+// stays an independent check of any later full recompute.  A lattice with no
+// model yet takes its base when the model is set.
 smcx_status restart_running_energy(smcx_lattice* lat) {
   SMCX_CUDA(lat, cudaMemsetAsync(lat->stats(), 0, sizeof(unsigned long long) * 16, lat->stream));
   lat->e0_known = false;
+  if (!lat->has_epi) return SMCX_OK;
+  int64_t e = 0;
+  const smcx_status s = full_energy(lat, &e);
+  if (s != SMCX_OK) return s;
+  lat->E0 = e;
+  lat->e0_known = true;
   return SMCX_OK;
 }
 
@@ -1081,19 +1088,11 @@ smcx_status smcx_running_energy(smcx_lattice* lat, int64_t* e_q) {
   if (s != SMCX_OK) return s;
   if (!lat->has_epi) return fail(SMCX_ESTATE, "no EPI set");
   if (!e_q) return fail(SMCX_EINVAL, "null output");
-  int64_t e_now = 0;
-  if (!lat->e0_known) {
-    s = full_energy(lat, &e_now);
-    if (s != SMCX_OK) return s;
-  }
+  if (!lat->e0_known) return fail(SMCX_ESTATE, "running energy has no base");
   unsigned long long cum_de = 0;
   SMCX_CUDA(lat, cudaMemcpyAsync(&cum_de, lat->stats() + kStatCum + 3, sizeof(cum_de),
                                  cudaMemcpyDeviceToHost, lat->stream));
   SMCX_CUDA(lat, cudaStreamSynchronize(lat->stream));
-  if (!lat->e0_known) {
-    lat->E0 = static_cast<int64_t>(static_cast<uint64_t>(e_now) - cum_de);
-    lat->e0_known = true;
-  }
   *e_q = static_cast<int64_t>(static_cast<uint64_t>(lat->E0) + cum_de);
   return SMCX_OK;
 }

@@ -88,6 +88,7 @@ class Server:
             ticket, job, arr = self.running.pop(jid)
             r = self.batch.result(jid)
             self.batch.remove(jid)
+            r["job"] = job.get("job", ticket)
             r["latency_s"] = now - arr
             r["arrival_s"] = arr
             r["finish_s"] = now

@@ -1,10 +1,11 @@
-"""Long-run parity (the segment checks of a long anneal): the GPU runs a
-lattice through a 10^4-sweep linear anneal (1200 -> 600 K, the schedule of
-the 1.07e9-site workload) with checkpoints, and from the checkpoints at
-sweeps 0, 5000 and 9997 the oracle replays 3 sweeps that must end in the
-GPU's bits.  On the 1.07e9-site lattice itself, where 3 oracle sweeps take
-far too long, sampled link cells of colour phases after 200 GPU sweeps are
-replayed instead."""
+"""Long-run parity (the segment checks of long runs): the GPU runs a lattice
+through a 10^4-sweep linear anneal (1200 -> 600 K, the schedule of the
+1.07e9-site workload) with checkpoints, and from the checkpoints at sweeps
+0, 5000 and 9997 the oracle replays 3 sweeps that must end in the GPU's
+bits; the FCC 128^3 workload runs its 1000 sweeps with oracle checks every
+100 sweeps and segment replays.  On the 1.07e9-site lattice itself sampled
+link cells of colour phases after 200 GPU sweeps are replayed (whole phases
+are in test_gpu_fullsize.py)."""
 import numpy as np
 import pytest
 
@@ -76,10 +77,13 @@ def test_bcc812_sampled_cells_after_200_sweeps(orc):
 
 def test_fcc128_k5_thousand_sweeps_with_sro_checks(orc):
     """FCC 128^3 x4 = 8.4e6 sites, K = 5 (Dirichlet(5) composition), shells
-    1-4, 800 K, 1000 sweeps: every 100 sweeps the running energy equals the
-    recomputed energy, the species counts are conserved and the SRO
-    parameters satisfy the sum rule; sampled link cells of two colour phases
-    of sweep 1000 match the oracle."""
+    1-4, 800 K, 1000 sweeps on the GPU.  Every 100 sweeps the SRO pair counts
+    equal the oracle's counts of the GPU's occupancy (and satisfy the sum
+    rule), the full energy equals the oracle's and the running energy (its
+    base taken at set_epi), and the species counts are conserved.  From the
+    GPU's states at sweeps 0, 500 and 997 the oracle replays 3 sweeps (cells
+    of each colour over all host cores) that end in the GPU's bits with the
+    same per-sweep statistics."""
     require_cuda()
     from paper_2509_20949_gb300 import inputs
     w = inputs.workload("fcc128_k5")
@@ -87,27 +91,37 @@ def test_fcc128_k5_thousand_sweeps_with_sro_checks(orc):
                      epi_seed=w["epi_seed"], occ_seed=w["occ_seed"], fractions=w["fractions"])
     lat = gpu_lattice(case)
     d = oracle_desc(orc, case)
+    T = w["T_first"]
     counts0 = np.bincount(case["occ"], minlength=w["K"])
     c = counts0 / counts0.sum()
-    for block in range(10):
-        lat.sweep(100, w["T_first"])
-        assert lat.running_energy() == lat.energy()
-        cnt, alpha = lat.sro(w["M"])
-        assert np.array_equal(cnt.sum(axis=(1, 2)),
-                              counts0.sum() * np.array([12, 6, 24, 12], dtype=np.uint64))
-        for m in range(w["M"]):
-            assert np.allclose(alpha[m] @ c, 0.0, atol=1e-12)  # sum_p c_p alpha^{pp'} = 0
-    occ = lat.occupancy()
-    assert np.array_equal(np.bincount(occ, minlength=w["K"]), counts0)
-    rng = np.random.default_rng(29)
-    for colour in (2, 7):
-        lat.run_colour(colour, w["T_first"])
-        after = lat.occupancy()
-        pick = np.sort(rng.choice(colour_cells(orc, d, colour), 3000, replace=False)).astype(np.uint32)
-        o_occ, _ = orc.phase_cells(d, case["V"], occ, 1000, w["T_first"], colour, pick)
-        sites = write_region_sites(orc, d, 1000, pick)
-        assert np.array_equal(after[sites], o_occ[sites]), colour
-        occ = after
+    seg_starts = (0, 500, 997)
+    marks = sorted((set(range(100, 1001, 100)) | set(seg_starts) | {a + 3 for a in seg_starts})
+                   - {0})
+    states, seg_stats, t = {0: case["occ"]}, {}, 0
+    for mark in marks:
+        st = lat.sweep(mark - t, T)
+        if t in seg_starts:
+            assert mark == t + 3
+            seg_stats[t] = st
+        t = mark
+        if t in seg_starts or t - 3 in seg_starts:
+            states[t] = lat.occupancy()
+        if t % 100 == 0:
+            occ = lat.occupancy()
+            assert np.array_equal(np.bincount(occ, minlength=w["K"]), counts0)
+            cnt, alpha = lat.sro(w["M"])
+            assert np.array_equal(cnt, orc.pair_counts(d, occ)), t
+            E = lat.energy()
+            assert E == orc.energy(d, case["V"], occ) == lat.running_energy(), t
+            for m in range(w["M"]):
+                assert np.allclose(alpha[m] @ c, 0.0, atol=1e-12)  # sum_p c_p alpha^{pp'} = 0
+    assert lat.sweep_counter == 1000
+    for a in seg_starts:
+        o_occ, o_st = orc.sweeps_par(d, case["V"], states[a], a, 3, T)
+        assert np.array_equal(o_occ, states[a + 3]), a
+        g = seg_stats[a]
+        assert (g["attempts"], g["unlike"], g["accepted"], g["sum_dE"]) == tuple(
+            int(o_st[k].sum()) for k in ("attempts", "unlike", "accepted", "sum_dE")), a
 
 
 def test_bcc812_packed_storage_equals_bytes():

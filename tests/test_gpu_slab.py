@@ -1,8 +1,9 @@
 """z decomposition on the GPU (Sec. 2.2, lattice parallelism): plane copies
-and merges of libsmcx.so, one rank equal to smcx_sweep, and two ranks (two
-processes sharing one GPU, boundary planes host-staged over gloo; no kernel
-waits on another process) whose gathered lattice and summed statistics equal
-the single-lattice sweeps bit for bit, for each sweep kernel."""
+and merges of libsmcx.so, one rank equal to smcx_sweep, and two or three
+ranks (processes sharing one GPU, boundary planes host-staged over gloo; no
+kernel waits on another process) whose gathered lattice and summed
+statistics equal the oracle's single-lattice sweeps bit for bit, for each
+sweep kernel."""
 import os
 import socket
 
@@ -10,7 +11,7 @@ import numpy as np
 import pytest
 import torch.multiprocessing as mp
 
-from tests.gpu_util import gpu_lattice, make_case, require_cuda
+from tests.gpu_util import gpu_lattice, make_case, oracle_desc, require_cuda
 
 pytestmark = pytest.mark.gpu
 
@@ -89,7 +90,7 @@ def _worker(rank, world, port, case, pack_bits, kernel, q):
     (0, (14, 10, 27), 6, 2, 4, 0, 2),   # BCC, 4-bit storage, ragged z cells
     (1, (10, 9, 21), 3, 4, 8, 1, 2),    # FCC shells 1-4, generic kernel, ragged
 ])
-def test_ranks_reproduce_the_single_lattice(kind, n, K, M, pack_bits, kernel, world):
+def test_ranks_reproduce_the_single_lattice(orc, kind, n, K, M, pack_bits, kernel, world):
     require_cuda()
     case = make_case(kind, n, K, M, seed=7, epi_seed=8, occ_seed=9)
     ctx = mp.get_context("spawn")
@@ -103,9 +104,13 @@ def test_ranks_reproduce_the_single_lattice(kind, n, K, M, pack_bits, kernel, wo
     for p in procs:
         p.join(timeout=120)
         assert p.exitcode == 0
-    ref = gpu_lattice(case, pack_bits=pack_bits, kernel=kernel)
-    want = [ref.sweep(nsw, a, b) for nsw, a, b in SCHEDULE]
-    occ = ref.occupancy()
+    # the oracle's single-lattice sweeps over the same schedule
+    d = oracle_desc(orc, case)
+    occ, t0, want = case["occ"], 0, []
+    for nsw, a, b in SCHEDULE:
+        occ, st = orc.sweeps(d, case["V"], occ, t0, nsw, a, b)
+        t0 += nsw
+        want.append({k: int(st[k].sum()) for k in ("attempts", "unlike", "accepted", "sum_dE")})
     for rank, r_occ, stats, kin in res:
         if kernel:
             assert kin[0] == kernel
