@@ -49,6 +49,10 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="bcc812_k5")
     ap.add_argument("--kernel", type=int, default=0, help="0 auto, 1 generic, 2 tiled")
+    ap.add_argument("--tile", type=int, default=-1,
+                    help="tile shape of the tiled kernel (-1: the online choice)")
+    ap.add_argument("--staging", type=int, default=0,
+                    help="tiled kernel staging: 0 bulk (TMA) copies where they fit, 1 cp.async only")
     ap.add_argument("--pack-bits", type=int, default=8)
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -693,6 +697,10 @@ def main():
                   stream=stream)
     if args.kernel:
         lat.set_option(1, args.kernel)
+    if args.tile >= 0:
+        lat.set_option(2, args.tile)
+    if args.staging:
+        lat.set_option(3, args.staging)
     lat.set_epi(V)
     M = w["M"]
 
@@ -765,7 +773,8 @@ def main():
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(w, N, V, occ, args.cpu_seconds, rank)
-    rec = _recorded_profile() if args.workload == "bcc812_k5" and args.pack_bits == 8 else None
+    rec = (_recorded_profile(N) if args.workload in ("bcc812_k5", "bcc448_k5") and args.pack_bits == 8
+           and args.staging == 0 else None)
     traffic = rec["dram_bytes_per_launch"] if rec else None
     # unlike and accepted fractions of the trials of one more sweep (outside the timed region)
     ts = lat.sweep(1, sweep_temperature(w, args.warmup + args.steps + args.e2e_steps))
@@ -816,14 +825,16 @@ def main():
     return 0
 
 
-def _recorded_profile():
-    """Figures of the committed ncu summary of the tiled sweep phase (DRAM
-    bytes per launch, shared-memory pipe and issue utilisation), if it was
-    taken on the current kernel source (else None)."""
+def _recorded_profile(n_sites):
+    """Figures of the committed ncu summary of the tiled sweep phase, if it
+    was taken on the current kernel source (else None): the DRAM bytes of
+    one phase scaled from the profiled lattice to n_sites sites (a phase
+    stages the whole lattice with its halos once, so the traffic grows with
+    the sites), and the shared-memory-pipe and issue utilisation."""
     import hashlib
     import re
 
-    prof = os.path.join(ROOT, "profiles", "sweep_tiled_bcc812_k5.md")
+    prof = os.path.join(ROOT, "profiles", "sweep_tiled_bcc448_k5.md")
     src = os.path.join(ROOT, "paper_2509_20949_gb300", "csrc", "kernels_tiled.cuh")
     try:
         text = open(prof).read()
@@ -832,21 +843,22 @@ def _recorded_profile():
         return None
     m_sha = re.search(r"source_sha1 \(.*?\): ([0-9a-f]+)", text)
     m_b = re.search(r"dram_bytes_per_launch: ([0-9]+)", text)
-    if not m_sha or not m_b or m_sha.group(1) != sha:
+    m_n = re.search(r"^sites: ([0-9]+)", text, re.M)
+    if not m_sha or not m_b or not m_n or m_sha.group(1) != sha:
         return None
-    out = {"dram_bytes_per_launch": int(m_b.group(1))}
+    out = {"dram_bytes_per_launch": int(m_b.group(1)) * n_sites // int(m_n.group(1)),
+           "profiled_sites": int(m_n.group(1))}
     m_s = re.search(r"shared wavefronts \| [0-9.]+M \(([0-9.]+)% of the shared pipe", text)
     m_i = re.search(r"\| issue active \| ([0-9.]+)%", text)
     if m_s and m_i:
-        out["limiter"] = {"unit": "shared-memory pipe", "frac": float(m_s.group(1)) / 100.0,
+        out["limiter"] = {"unit": "latency of the trial's dependent chain (shared pipe and issue "
+                                  "both below saturation)",
+                          "shared_pipe_frac": float(m_s.group(1)) / 100.0,
                           "issue_active_frac": float(m_i.group(1)) / 100.0,
-                          "source": "profiles/sweep_tiled_bcc812_k5.md"}
+                          "source": "profiles/sweep_tiled_bcc448_k5.md"}
     return out
 
 
-def _recorded_traffic():
-    rec = _recorded_profile()
-    return rec["dram_bytes_per_launch"] if rec else None
 
 
 if __name__ == "__main__":

@@ -327,9 +327,15 @@ smcx_status smcx_restore(smcx_lattice* lat, const void* buf, size_t len);
                        cannot run the lattice).  Under the local-energy
                        model every sweep runs its own kernel, reported as 4
                        by smcx_kernel_in_use, whatever this option says
-     SMCX_OPT_TILE     index of the tile shape among smcx_tile_shape(...) */
+     SMCX_OPT_TILE     index of the tile shape among smcx_tile_shape(...)
+     SMCX_OPT_STAGING  how the tiled kernel fills its shared-memory tiles:
+                       0 = one bulk (TMA) copy per tile row wherever the
+                       row's 16-byte aligned span fits (default), 8-byte
+                       cp.async copies elsewhere; 1 = 8-byte cp.async copies
+                       only */
 #define SMCX_OPT_KERNEL 1u
 #define SMCX_OPT_TILE 2u
+#define SMCX_OPT_STAGING 3u
 smcx_status smcx_set_option(smcx_lattice* lat, uint32_t key, int64_t value);
 
 /* Number of tile shapes compiled for a lattice kind and the cells per tile

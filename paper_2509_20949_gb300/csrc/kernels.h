@@ -41,19 +41,27 @@ bool tiled_supported(const Geom& g, int shape);
 int tiled_shape_count(int kind);
 void tiled_shape_cells(int kind, int shape, int cells[3]);
 
-// Layout of the tiled kernel's difference rows, shared by the host table
-// builder and the kernel: row (sigma_p, sigma_q) at byte
-// (sigma_p * kmax + sigma_q) * tiled_row_bytes, int32 D'[m][s - 1] at its
-// start and the int64 constant C at tiled_doff_c.
-__host__ __device__ constexpr int tiled_code_width(int kmax) { return kmax <= 5 ? 6 : 5; }
+// Layout of the difference rows of the tiled and cell kernels, shared by
+// the host table builder and the kernels: row (sigma_p, sigma_q) at byte
+// (sigma_p * kmax + sigma_q) * tiled_row_bytes, the int64 constant C at
+// tiled_doff_c.  K <= 5 (kmax 5, storage codes 8 sigma): per shell m one
+// 16-byte word group, word t holding byte t of D'_{m,s} for s = 0..3
+// (delta_e_dp4a).  K = 6 (kmax 6, codes 5 sigma): int32 D'[m][s - 1].
+__host__ __device__ constexpr int tiled_code_width(int kmax) { return kmax <= 5 ? 8 : 5; }
 __host__ __device__ constexpr int tiled_doff_c(int M, int kmax) {
   return (4 * M * (kmax - 1) + 7) / 8 * 8;
 }
-// rows are 16-byte aligned (vector loads): rstep * W must be a multiple of 16
+// rows are 16-byte aligned (vector loads): rstep * W must be a multiple of
+// 16.  With W = 8 the row is an odd number of 16-byte words, so the rows of
+// the (p, q) pairs that the lanes of a warp pick at random start at eight
+// different bank offsets (fewer conflicts in their 16-byte loads).
 __host__ __device__ constexpr int tiled_row_bytes(int M, int kmax) {
   const int W = tiled_code_width(kmax);
-  const int q = W == 6 ? 8 : 16;
-  const int rstep = ((tiled_doff_c(M, kmax) + 8 + W - 1) / W + q - 1) / q * q;
+  if (W == 8) {
+    const int words = (tiled_doff_c(M, kmax) + 8 + 15) / 16;
+    return 16 * (words % 2 ? words : words + 1);
+  }
+  const int rstep = ((tiled_doff_c(M, kmax) + 8 + W - 1) / W + 15) / 16 * 16;
   return rstep * W;
 }
 

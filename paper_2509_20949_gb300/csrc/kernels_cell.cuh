@@ -39,7 +39,7 @@ struct CCfg {
   static constexpr int KIND = KIND_, M = M_, KMAX = KMAX_;
   static constexpr bool INLINE_KEYS = INLINE_KEYS_;
   static constexpr int NB = KIND == 0 ? 2 : 4;
-  static constexpr int W = KMAX <= 5 ? 6 : 5;
+  static constexpr int W = KMAX <= 5 ? 8 : 5;
   static constexpr int Z1 = shell_z(KIND, 0);
   static constexpr int DOFF_C = tiled_doff_c(M, KMAX);
   static constexpr int ROWB = tiled_row_bytes(M, KMAX);
@@ -103,7 +103,7 @@ template <class C, int B, int S, int LO, int HI>
 __device__ __forceinline__ uint32_t csum_i(const uint8_t* occ, const Coords& T, const uint32_t* bofs) {
   if constexpr (HI - LO == 1) {
     using N = CNbr<C, B, S + LO>;
-    return 1u << occ[T.x[N::ix] + T.y[N::iy] + T.z[N::iz] + bofs[N::bp]];
+    return onehot(occ[T.x[N::ix] + T.y[N::iy] + T.z[N::iz] + bofs[N::bp]]);
   } else {
     constexpr int MID = (LO + HI) / 2;
     return csum_i<C, B, S, LO, MID>(occ, T, bofs) + csum_i<C, B, S, MID, HI>(occ, T, bofs);
@@ -120,7 +120,7 @@ __device__ __forceinline__ uint32_t csum_j_fcc(const uint8_t* occ, const Coords&
     const uint32_t ax = N::ox ? To.x[N::ix] : T.x[N::ix];
     const uint32_t ay = N::oy ? To.y[N::iy] : T.y[N::iy];
     const uint32_t az = N::oz ? To.z[N::iz] : T.z[N::iz];
-    return 1u << occ[ax + ay + az + cls_ofs[N::cls]];
+    return onehot(occ[ax + ay + az + cls_ofs[N::cls]]);
   } else {
     constexpr int MID = (LO + HI) / 2;
     return csum_j_fcc<C, S, LO, MID>(occ, T, To, cls_ofs) + csum_j_fcc<C, S, MID, HI>(occ, T, To, cls_ofs);
@@ -239,32 +239,28 @@ __device__ __forceinline__ void run_cell(const Geom& g, uint8_t* __restrict__ oc
           const bool unlike = p != q;
           *n_unl += unlike;
           const uint8_t* row = s_d + (p * C::KMAX + q) * C::RSTEP;
-          constexpr int ND = C::M * (C::KMAX - 1);
-          int32_t dr[(ND + 3) / 4 * 4];
+          long long de;
+          if constexpr (C::KMAX <= 5) {
+            de = delta_e_dp4a<C::M, C::DOFF_C>(acc_i, acc_j, row);
+          } else {
+            constexpr int ND = C::M * (C::KMAX - 1);
+            int32_t dr[(ND + 3) / 4 * 4];
 #pragma unroll
-          for (int v = 0; v < (ND + 3) / 4; ++v) {
-            const int4 d4 = reinterpret_cast<const int4*>(row)[v];
-            dr[4 * v] = d4.x;
-            dr[4 * v + 1] = d4.y;
-            dr[4 * v + 2] = d4.z;
-            dr[4 * v + 3] = d4.w;
-          }
-          long long de = -*reinterpret_cast<const long long*>(row + C::DOFF_C);
+            for (int v = 0; v < (ND + 3) / 4; ++v) {
+              const int4 d4 = reinterpret_cast<const int4*>(row)[v];
+              dr[4 * v] = d4.x;
+              dr[4 * v + 1] = d4.y;
+              dr[4 * v + 2] = d4.z;
+              dr[4 * v + 3] = d4.w;
+            }
+            de = -*reinterpret_cast<const long long*>(row + C::DOFF_C);
 #pragma unroll
-          for (int m = 0; m < C::M; ++m) {
-            if constexpr (C::KMAX <= 5) {
-              const uint32_t F = 0x20820820u + acc_i[m] - acc_j[m];
-#pragma unroll
-              for (int s = 1; s < C::KMAX; ++s)
-                de += static_cast<long long>(static_cast<int>((F >> (6 * s)) & 63u)) *
-                      static_cast<long long>(dr[m * (C::KMAX - 1) + s - 1]);
-            } else {
+            for (int m = 0; m < C::M; ++m)
 #pragma unroll
               for (int s = 1; s < C::KMAX; ++s)
                 de += static_cast<long long>(static_cast<int>((acc_i[m] >> (5 * s)) & 31u) -
                                              static_cast<int>((acc_j[m] >> (5 * s)) & 31u)) *
                       static_cast<long long>(dr[m * (C::KMAX - 1) + s - 1]);
-            }
           }
           const uint64_t idx = static_cast<uint64_t>(de) >> sbin;
           const uint32_t i2 = idx >> 18 < 511u ? static_cast<uint32_t>(idx >> 18) : 511u;

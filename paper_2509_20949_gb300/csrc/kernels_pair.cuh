@@ -52,8 +52,8 @@ struct PCfg {
   static constexpr int RS = NB * XW;
   static constexpr int PS = RS * TY;
   static constexpr int TILE = PS * TZ;
-  static constexpr int W = KMAX <= 5 ? 6 : 5;       // tile code = sigma * W
-  static constexpr int FW = 2 * W;                  // accumulator field width
+  static constexpr int W = KMAX <= 5 ? 8 : 5;       // tile code = sigma * W
+  static constexpr int FW = W == 8 ? 12 : 2 * W;    // accumulator field width (FW sigma = shift)
   static constexpr int NT = 128;
   static constexpr int G = PACK4 ? NB / 2 : NB;
   static constexpr int NCNT = M * KMAX * KMAX;
@@ -69,10 +69,17 @@ __host__ __device__ constexpr int poff(int b, int v) {
          (bp - b) * C::XW;
 }
 
+// bit position FW sigma of the field of the species with tile code c = W sigma
+template <class C>
+__device__ __forceinline__ uint32_t field_shift(uint32_t c) {
+  if constexpr (C::W == 8) return c + (c >> 1);
+  else return 2u * c;
+}
+
 template <class C, int B, int Mm, int... I>
 __device__ __forceinline__ unsigned long long half_shell(const uint8_t* base,
                                                          std::integer_sequence<int, I...>) {
-  return (0ull + ... + (1ull << (2u * base[poff<C>(B, pos_vec(C::KIND, Mm, I))])));
+  return (0ull + ... + (1ull << field_shift<C>(base[poff<C>(B, pos_vec(C::KIND, Mm, I))])));
 }
 
 template <class C, int B, int... Ms>

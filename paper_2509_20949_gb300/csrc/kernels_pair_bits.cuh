@@ -40,7 +40,7 @@ struct BCfg {
   static constexpr int NB = KIND == 0 ? 2 : 4;
   static constexpr int NQ = KMAX - 1;            // masks of species 0 .. KMAX - 2
   static constexpr int NQC = NQ <= 4 ? 1 : 2;    // 16-byte chunks of masks per span and plane
-  static constexpr int W = KMAX <= 5 ? 6 : 5;    // storage code = sigma * W
+  static constexpr int W = KMAX <= 5 ? 8 : 5;    // storage code = sigma * W
   static constexpr int H = (KIND == 0 && M == 4) ? 2 : 1;  // halo rows; x offsets 0..H
   static constexpr int SW = 16 * NQC;            // words per span: 4 planes x NQC chunks
   static constexpr int NT = 256;

@@ -5,26 +5,32 @@
 // concurrently because they never touch one another's interaction zones.
 // A block owns BX x BY x BZ active cells of the phase; it stages their
 // cells plus a two-conventional-cell halo (the local interaction zone of
-// every trial, Sec. 2.2) from HBM into shared memory with 8-byte vector
-// loads, runs the trials on the shared tile and stores every accepted swap
-// straight back to HBM (global addresses follow the loop counters; tiles that
-// cross a periodic seam decompose the shared offset instead).
+// every trial, Sec. 2.2) from HBM into shared memory -- one bulk (TMA) copy
+// per tile sub-row, completed on an mbarrier, where the sub-row's 16-byte
+// aligned span fits the tile row; 8-byte cp.async copies otherwise; byte
+// loads for tiles across the periodic x seam -- and runs the trials on the
+// shared tile.  An accepted swap is stored to HBM at once (8-bit storage,
+// 32-bit offsets that follow the loop counters); tiles across a periodic
+// seam and packed storage instead store the part of the tile their trials
+// can have changed back to HBM at the end.
 //
 // Energy change of a trial (EPI model, Sec. 3): with p = sigma_i, q = sigma_j,
 //   dE = sum_m sum_s dx_{m,s} (V_m(q,s) - V_m(p,s)) - (V_1(p,p)+V_1(q,q)-2V_1(p,q)),
 // where dx_{m,s} = (# shell-m neighbours of i of species s) - (same for j):
 // the neighbour species are counted with one-hot SWAR adds (each shared
-// memory byte holds sigma*W, the bit position of species sigma in a W-bit
-// field), the i-j bond, counted once from each side, is removed by the last
-// term.  Because sum_s dx_{m,s} = 0 the s = 0 column folds into the others,
-// and for K <= 5 the two count words are subtracted field-wise with a bias of
-// 32 per field; the constants that leaves are precomputed per (p, q).
+// memory byte holds sigma*W, the bit position of species sigma in the count
+// word), the i-j bond, counted once from each side, is removed by the last
+// term.  Because sum_s dx_{m,s} = 0 one species' column folds into the
+// others.  K <= 5 (W = 8): byte s counts species s, species 4 shifts out, and
+// the two count words meet in four byte dot products per shell
+// (delta_e_dp4a); K = 6 (W = 5): 5-bit fields, species 0 folded.
 //
 // Shared tile layout: rows (z, y) of pitch RS holding NB sub-rows (one per
-// basis site b) of pitch XW; byte x of sub-row b is site (x, y, z, b).  RS is
-// congruent to 16 modulo 32 bytes so that the 32 lanes of a warp (16 cells
-// along x, 2 along y, cells 2L conventional cells apart) hit 32 distinct
-// banks for every neighbour load.  Shared offsets of every neighbour are
+// basis site b) of pitch XW; byte x of sub-row b is site (x, y, z, b).  With
+// warps of 16 cells along x and 2 along y (cells 2L conventional cells
+// apart) RS is congruent to 16 modulo 32 bytes, so the 32 lanes hit 32
+// distinct banks for every anchor-side neighbour load; warps of 32 cells
+// along x take the pitches described at Cfg::RS.  Shared offsets of every neighbour are
 // compile-time constants (the anchor's basis is unrolled); the partner's
 // basis is fixed for BCC and taken from four class bases for FCC.
 #pragma once
@@ -75,10 +81,20 @@ struct Cfg {
   static constexpr int EXT_Z = (2 * BZ - 1) * L + SLACK + 2 * H;
   static constexpr int XW = round_up(EXT_X + 14, 8);  // 8-byte copy alignment slack
   static constexpr int RS0 = NB * XW;
+  // Row and plane pitches.  Warps of 16 x 2 cells: RS = 16 mod 32 bytes puts
+  // the two y lanes of a warp 16 banks apart.  Warps of 32 cells along x
+  // (BX = 32) cover all 32 banks with their anchors whatever the pitches,
+  // which are then chosen for the partner side: RS = 64 mod 128 and PS = 0
+  // mod 128, so a partner one row or plane away moves a lane by 0 or 16
+  // banks (at most two-way conflicts; a partner one byte away in x stays in
+  // its own or the next lane's word).
+  static constexpr bool WIDE = BX == 32;
   static constexpr int BANK = BX >= 16 ? 16 : BX;     // lane spacing of the y lanes in banks
-  static constexpr int RS = RS0 + (((BANK - RS0 % 32) % 32) + 32) % 32;
-  static constexpr int PS = RS * EXT_Y;
-  static constexpr int W = KMAX <= 5 ? 6 : 5;
+  static constexpr int RS_W = round_up(RS0, 64) % 128 == 0 ? round_up(RS0, 64) + 64
+                                                           : round_up(RS0, 64);
+  static constexpr int RS = WIDE ? RS_W : RS0 + (((BANK - RS0 % 32) % 32) + 32) % 32;
+  static constexpr int PS = WIDE ? round_up(RS * EXT_Y, 128) : RS * EXT_Y;
+  static constexpr int W = KMAX <= 5 ? 8 : 5;
   static constexpr int NT = BX * BY * BZ;
   // resident blocks per SM the register budget must allow (shared memory
   // admits about as many)
@@ -93,9 +109,12 @@ struct Cfg {
   static constexpr int RSTEP = ROWB / W;
   static constexpr int DBYTES = KMAX * KMAX * ROWB;
   static constexpr int G = PACK4 ? NB / 2 : NB;                   // device row groups
-  static constexpr int GPART_OFF = round_up(4 * kTabWords + DBYTES + 4 * NB * Z1, 8);
-  static constexpr int TILE_OFF = round_up(GPART_OFF + 8 * NB * Z1, 16);  // bytes before the tile
-  static_assert(RS % 32 == BANK % 32, "bank padding");
+  static constexpr int MBAR_OFF = round_up(4 * kTabWords + DBYTES + 8 * NB * Z1, 8);
+  static constexpr int TILE_OFF = round_up(MBAR_OFF + 8, 16);  // bytes before the tile
+  // sub-rows can be bulk-copied (16-byte aligned destinations) when every
+  // pitch is a multiple of 16 bytes
+  static constexpr bool BULK = XW % 16 == 0 && RS % 16 == 0 && PS % 16 == 0;
+  static_assert(WIDE ? (RS % 128 == 64 && PS % 128 == 0) : RS % 32 == BANK % 32, "bank padding");
   static_assert(RS % 8 == 0 && XW % 8 == 0, "8-byte alignment of the tile rows");
 };
 
@@ -140,7 +159,7 @@ __host__ __device__ constexpr int corr_of(int b, int cls) {
 template <class C, int B, int S, int LO, int HI>
 __device__ __forceinline__ uint32_t count_i(const uint8_t* base) {
   if constexpr (HI - LO == 1) {
-    return 1u << base[NbrOff<C, B, S + LO>::value];
+    return onehot(base[NbrOff<C, B, S + LO>::value]);
   } else {
     constexpr int MID = (LO + HI) / 2;
     return count_i<C, B, S, LO, MID>(base) + count_i<C, B, S, MID, HI>(base);
@@ -150,7 +169,7 @@ __device__ __forceinline__ uint32_t count_i(const uint8_t* base) {
 template <class C, int S, int LO, int HI>
 __device__ __forceinline__ uint32_t count_j_fcc(const uint8_t* const* cls_base) {
   if constexpr (HI - LO == 1) {
-    return 1u << cls_base[Off0<C, S + LO>::cls][Off0<C, S + LO>::value];
+    return onehot(cls_base[Off0<C, S + LO>::cls][Off0<C, S + LO>::value]);
   } else {
     constexpr int MID = (LO + HI) / 2;
     return count_j_fcc<C, S, LO, MID>(cls_base) + count_j_fcc<C, S, MID, HI>(cls_base);
@@ -205,20 +224,70 @@ __device__ __forceinline__ void partner_shift(int b, int dir, int* dx, int* dy, 
                         std::make_integer_sequence<int, C::NB * C::Z1>{});
 }
 
-
-__device__ __forceinline__ int wrapn(int v, int n) {
-  v %= n;
-  return v < 0 ? v + n : v;
-}
-
-// sigma of each byte of a word of codes sigma * W (sigma <= 5): per 16-bit lane
-// (code * ceil(256 / W)) >> 8, exact for codes <= 30
+// sigma of each byte of a word of codes sigma * W: W = 8 a shift; W = 5
+// (sigma <= 5) per 16-bit lane (code * 52) >> 8, exact for codes <= 25
 template <int W>
 __device__ __forceinline__ uint32_t codes_to_sigma(uint32_t w) {
-  constexpr uint32_t mul = W == 6 ? 43u : 52u;
-  const uint32_t even = (((w & 0x00FF00FFu) * mul) >> 8) & 0x00FF00FFu;
-  const uint32_t odd = ((((w >> 8) & 0x00FF00FFu) * mul) >> 8) & 0x00FF00FFu;
-  return even | (odd << 8);
+  if constexpr (W == 8) {
+    return (w >> 3) & 0x1F1F1F1Fu;
+  } else {
+    const uint32_t even = (((w & 0x00FF00FFu) * 52u) >> 8) & 0x00FF00FFu;
+    const uint32_t odd = ((((w >> 8) & 0x00FF00FFu) * 52u) >> 8) & 0x00FF00FFu;
+    return even | (odd << 8);
+  }
+}
+template <int W>
+__device__ __forceinline__ uint32_t code_to_sigma(uint32_t c) {
+  if constexpr (W == 8) return c >> 3;
+  else return (c * 52u) >> 8;
+}
+
+// ---- bulk copies (TMA) completed on an mbarrier --------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(bar), "r"(count) : "memory");
+  // make the initialised barrier visible to the bulk-copy (async) proxy
+  asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+}
+// arrival of the barrier's single expected arrival, announcing `bytes` of
+// copies that complete on it
+__device__ __forceinline__ void mbar_arrive_expect(uint32_t bar, uint32_t bytes) {
+  asm volatile("{\n .reg .b64 st;\n mbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n}\n"
+               ::"r"(bar), "r"(bytes) : "memory");
+}
+// global -> shared bulk copy: both addresses 16-byte aligned, bytes a
+// multiple of 16
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes,
+                                         uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n"
+      ::"r"(dst), "l"(src), "r"(bytes), "r"(bar) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
+  uint32_t done;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(done) : "r"(bar), "r"(parity) : "memory");
+  return done != 0;
+}
+__device__ __forceinline__ unsigned long long tiled_globaltimer() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+// waits for phase `parity` of the barrier, giving up after about a second
+// (%globaltimer) or 2^24 polls; returns whether it completed
+__device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity) {
+  const unsigned long long t0 = tiled_globaltimer();
+  for (uint32_t i = 0; i < (1u << 24); ++i) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if ((i & 63u) == 63u && tiled_globaltimer() - t0 > 1000000000ull) break;
+  }
+  return false;
 }
 
 template <class C>
@@ -232,7 +301,8 @@ __global__ void __launch_bounds__(C::NT, C::MINB) k_sweep_tiled(const __grid_con
   uint32_t* s_tab = reinterpret_cast<uint32_t*>(smem);                      // 1536 words
   uint8_t* s_d = smem + 4 * kTabWords;                                      // DBYTES
   int* s_part = reinterpret_cast<int*>(s_d + C::DBYTES);                    // NB * Z1
-  long long* s_gpart = reinterpret_cast<long long*>(smem + C::GPART_OFF);    // NB * Z1
+  int* s_gpart = s_part + C::NB * C::Z1;                                    // NB * Z1
+  uint64_t* s_bar = reinterpret_cast<uint64_t*>(smem + C::MBAR_OFF);        // staging barrier
   uint8_t* tile = smem + C::TILE_OFF;
 
   const int tid = threadIdx.x;
@@ -256,24 +326,33 @@ __global__ void __launch_bounds__(C::NT, C::MINB) k_sweep_tiled(const __grid_con
     v -= v >= g.n[d] ? g.n[d] : 0;
     g0[d] = v;
   }
-  const int off = g0[0] & 7;
   const bool wrap_x = g0[0] + ext[0] > g.n[0];
   const bool wrap_any = wrap_x || g0[1] + ext[1] > g.n[1] || g0[2] + ext[2] > g.n[2];
+  // device storage: rows of px bytes, the z step and the basis-row step
+  const long long zstr = static_cast<long long>(g.n[1]) * g.px;
+  const long long gstr = zstr * g.n[2];
+  // accepted swaps are stored at once with 32-bit offsets (8-bit storage, no
+  // wrap, fewer than 2^31 bytes of storage); otherwise the tile is written
+  // back at the end
+  const bool direct = !C::PACK4 && !wrap_any && gstr * C::NB < (1ll << 31);
+  // staging: bulk copies of the 16-byte aligned span of each sub-row when
+  // it fits the tile row, else 8-byte copies; the tile's x origin `off` is
+  // the global x of its first site modulo the copy alignment
+  const bool bulk = C::BULK && a.staging == 0 && !wrap_x && (g0[0] & 15) + ext[0] <= C::XW;
+  const int off = bulk ? (g0[0] & 15) : (g0[0] & 7);
 
   // ---- tables ------------------------------------------------------------
   for (int w = tid; w < kTabWords; w += C::NT) s_tab[w] = tab.w[w];
   for (int w = tid; w < C::DBYTES / 4; w += C::NT)
     reinterpret_cast<uint32_t*>(s_d)[w] = dtab[w];
   if (tid == 0) fill_partner_table<C>(s_part, std::make_integer_sequence<int, C::NB * C::Z1>{});
-  // device-storage offset of the partner (no periodic wrap): conventional
-  // cell offsets along x, y, z and the change of basis (8-bit storage)
-  const long long zstr = static_cast<long long>(g.n[1]) * g.px;          // z step
-  const long long gstr = zstr * g.n[2];                                  // basis-row step
+  // storage offset of the partner from its anchor (8-bit storage, no wrap)
   if (tid < C::NB * C::Z1) {
     const int b = tid / C::Z1, dir = tid % C::Z1;
     int dx = 0, dy = 0, dz = 0, bj = 0;
     partner_shift<C>(b, dir, &dx, &dy, &dz, &bj);
-    s_gpart[tid] = dx + dy * static_cast<long long>(g.px) + dz * zstr + (bj - b) * gstr;
+    s_gpart[tid] = static_cast<int>(dx + dy * static_cast<long long>(g.px) + dz * zstr +
+                                    (bj - b) * gstr);
   }
 
   // ---- stage the tile ----------------------------------------------------
@@ -288,8 +367,8 @@ __global__ void __launch_bounds__(C::NT, C::MINB) k_sweep_tiled(const __grid_con
     *tz = static_cast<int>((static_cast<uint32_t>(t) * inv_ey) >> 16);
     *ty = t - *tz * ext_y;
   };
-  const int g0x = g0[0], g0y = g0[1], g0z = g0[2];
-  const int nx = g.n[0], ny = g.n[1], nz = g.n[2];
+  const int g0y = g0[1], g0z = g0[2];
+  const int ny = g.n[1], nz = g.n[2];
   const size_t px = static_cast<size_t>(g.px);
   auto grow = [=](int grp, int ty, int tz) -> size_t {
     int gy = g0y + ty;
@@ -298,7 +377,57 @@ __global__ void __launch_bounds__(C::NT, C::MINB) k_sweep_tiled(const __grid_con
     gz -= gz >= nz ? nz : 0;
     return ((static_cast<size_t>(grp) * nz + gz) * ny + gy) * px;
   };
-  if (!wrap_x) {
+  if (bulk) {
+    // one bulk copy per sub-row (packed storage: the packed row lands in
+    // the odd basis's sub-row and is unpacked in place below)
+    const uint32_t bar = smem_u32(s_bar);
+    const uint32_t bytes = static_cast<uint32_t>(round_up(off + ext[0], 16));
+    if (tid == 0) {
+      mbar_init(bar, 1);
+      mbar_arrive_expect(bar, bytes * static_cast<uint32_t>(n_sub));
+    }
+    __syncthreads();
+    const uint8_t* src0 = occ + (g0[0] - off);
+    const uint32_t tbase = smem_u32(tile);
+    for (int sub = tid; sub < n_sub; sub += C::NT) {
+      int grp, ty, tz;
+      sub_row(sub, &grp, &ty, &tz);
+      const int slot = C::PACK4 ? 2 * grp + 1 : grp;
+      bulk_g2s(tbase + tz * C::PS + ty * C::RS + slot * C::XW, src0 + grow(grp, ty, tz), bytes,
+               bar);
+    }
+    bool done = mbar_wait_bounded(bar, 0);
+    if (!done) {
+      // report it, and do not leave while copies into this block's shared
+      // memory may still be in flight
+      atomicOr(stats + kStatWait, 1ull);
+      done = mbar_wait_bounded(bar, 0);
+    }
+    if (__syncthreads_or(!done)) return;  // the whole block leaves together
+    if constexpr (C::PACK4) {
+      // unpack 16 packed bytes (two sites each) per step: low nibbles to
+      // the even basis's sub-row, high nibbles in place
+      const int nc = static_cast<int>(bytes >> 4);  // 16-byte chunks per sub-row (<= 32)
+      const int rpi = 32 / nc;
+      const int my_r = lane / nc, my_c = lane - (lane / nc) * nc;
+      for (int base = warp * rpi; base < n_sub; base += NW * rpi) {
+        const int sub = base + my_r;
+        if (my_r >= rpi || sub >= n_sub) continue;
+        int grp, ty, tz;
+        sub_row(sub, &grp, &ty, &tz);
+        uint8_t* row = tile + tz * C::PS + ty * C::RS + 16 * my_c;
+        const uint4 v = *reinterpret_cast<const uint4*>(row + (2 * grp + 1) * C::XW);
+        const uint4 lo4 = make_uint4((v.x & 0x0F0F0F0Fu) * C::W, (v.y & 0x0F0F0F0Fu) * C::W,
+                                     (v.z & 0x0F0F0F0Fu) * C::W, (v.w & 0x0F0F0F0Fu) * C::W);
+        const uint4 hi4 = make_uint4(((v.x >> 4) & 0x0F0F0F0Fu) * C::W,
+                                     ((v.y >> 4) & 0x0F0F0F0Fu) * C::W,
+                                     ((v.z >> 4) & 0x0F0F0F0Fu) * C::W,
+                                     ((v.w >> 4) & 0x0F0F0F0Fu) * C::W);
+        *reinterpret_cast<uint4*>(row + (2 * grp) * C::XW) = lo4;
+        *reinterpret_cast<uint4*>(row + (2 * grp + 1) * C::XW) = hi4;
+      }
+    }
+  } else if (!wrap_x) {
     const int n8 = (off + ext[0] + 7) >> 3;  // 8-byte chunks per sub-row (<= 32)
     const int rpi = 32 / n8;                 // sub-rows per warp pass
     const int my_r = lane / n8, my_c = lane - (lane / n8) * n8;
@@ -374,31 +503,12 @@ __global__ void __launch_bounds__(C::NT, C::MINB) k_sweep_tiled(const __grid_con
     const uint32_t cid = (static_cast<uint32_t>(c[2]) * g.m[1] + c[1]) * g.m[0] + c[0];
     n_att = static_cast<uint32_t>(l[0] * l[1] * l[2] * C::NB);
 
-    // store of an accepted site by decomposing its shared offset toff
-    // (includes off): tiles that cross a periodic seam, and packed storage
-    auto store_slow = [&](int toff, uint32_t code) {
-      const int tz = toff / C::PS;
-      const int r1 = toff - tz * C::PS;
-      const int ty = r1 / C::RS;
-      const int r2 = r1 - ty * C::RS;
-      const int b = r2 / C::XW;
-      int gx = g0x + (r2 - b * C::XW - off);
-      gx -= gx >= nx ? nx : 0;
-      if constexpr (!C::PACK4) {
-        occ[grow(b, ty, tz) + gx] = static_cast<uint8_t>(code);
-      } else {
-        uint8_t* q = occ + grow(b >> 1, ty, tz) + gx;
-        const uint32_t sig = (code * (C::W == 6 ? 43u : 52u)) >> 8;
-        const uint32_t sh = (b & 1) * 4u;
-        *q = static_cast<uint8_t>((*q & ~(15u << sh)) | (sig << sh));
-      }
-    };
-    const bool fast_store = !C::PACK4 && !wrap_any;
-    // device address of this cell's first site (8-bit storage, no wrap)
-    uint8_t* const gcell = occ + (static_cast<long long>(g0z + o[2]) * ny + (g0y + o[1])) * px +
-                           (g0x + o[0]);
+    // storage offset of this cell's first site (direct stores only)
+    const uint32_t gcell = direct ? static_cast<uint32_t>(
+        (static_cast<long long>(g0[2] + o[2]) * g.n[1] + (g0[1] + o[1])) * g.px + (g0[0] + o[0]))
+        : 0u;
 
-    auto attempt = [&](auto bconst, int ai, uint8_t* gi, uint32_t wa, uint32_t wb) {
+    auto attempt = [&](auto bconst, int ai, uint32_t gi, uint32_t wa, uint32_t wb) {
       constexpr int B = decltype(bconst)::value;
       const uint32_t dir = __umulhi(wa, static_cast<uint32_t>(C::Z1));
       const int pt = s_part[B * C::Z1 + dir];
@@ -425,32 +535,28 @@ __global__ void __launch_bounds__(C::NT, C::MINB) k_sweep_tiled(const __grid_con
         count_all_j_fcc<C>(cls_base, acc_j, std::make_integer_sequence<int, C::M>{});
       }
       const uint8_t* row = s_d + (p * C::KMAX + q) * C::RSTEP;
-      constexpr int ND = C::M * (C::KMAX - 1);
-      int32_t dr[(ND + 3) / 4 * 4];
+      long long de;
+      if constexpr (C::KMAX <= 5) {
+        de = delta_e_dp4a<C::M, C::DOFF_C>(acc_i, acc_j, row);
+      } else {
+        constexpr int ND = C::M * (C::KMAX - 1);
+        int32_t dr[(ND + 3) / 4 * 4];
 #pragma unroll
-      for (int v = 0; v < (ND + 3) / 4; ++v) {
-        const int4 d4 = reinterpret_cast<const int4*>(row)[v];
-        dr[4 * v] = d4.x;
-        dr[4 * v + 1] = d4.y;
-        dr[4 * v + 2] = d4.z;
-        dr[4 * v + 3] = d4.w;
-      }
-      long long de = -*reinterpret_cast<const long long*>(row + C::DOFF_C);
+        for (int v = 0; v < (ND + 3) / 4; ++v) {
+          const int4 d4 = reinterpret_cast<const int4*>(row)[v];
+          dr[4 * v] = d4.x;
+          dr[4 * v + 1] = d4.y;
+          dr[4 * v + 2] = d4.z;
+          dr[4 * v + 3] = d4.w;
+        }
+        de = -*reinterpret_cast<const long long*>(row + C::DOFF_C);
 #pragma unroll
-      for (int m = 0; m < C::M; ++m) {
-        if constexpr (C::KMAX <= 5) {
-          const uint32_t F = 0x20820820u + acc_i[m] - acc_j[m];  // bias 32 per 6-bit field
-#pragma unroll
-          for (int s = 1; s < C::KMAX; ++s)
-            de += static_cast<long long>(static_cast<int>((F >> (6 * s)) & 63u)) *
-                  static_cast<long long>(dr[m * (C::KMAX - 1) + s - 1]);
-        } else {
+        for (int m = 0; m < C::M; ++m)
 #pragma unroll
           for (int s = 1; s < C::KMAX; ++s)
             de += static_cast<long long>(static_cast<int>((acc_i[m] >> (5 * s)) & 31u) -
                                          static_cast<int>((acc_j[m] >> (5 * s)) & 31u)) *
                   static_cast<long long>(dr[m * (C::KMAX - 1) + s - 1]);
-        }
       }
       // Metropolis (Sec. 2.1, Eq. 3) without branches: the table lookups are
       // clamped in range and only matter when dE > 0 in normal mode
@@ -463,12 +569,9 @@ __global__ void __launch_bounds__(C::NT, C::MINB) k_sweep_tiled(const __grid_con
       if (ok) {
         tile[ai] = static_cast<uint8_t>(q);
         tile[aj] = static_cast<uint8_t>(p);
-        if (fast_store) {
-          gi[0] = static_cast<uint8_t>(q);
-          gi[s_gpart[B * C::Z1 + dir]] = static_cast<uint8_t>(p);
-        } else {
-          store_slow(ai, q);
-          store_slow(aj, p);
+        if (direct) {
+          occ[gi] = static_cast<uint8_t>(q);
+          occ[gi + s_gpart[B * C::Z1 + dir]] = static_cast<uint8_t>(p);
         }
         ++n_acc;
         sum_de += de;
@@ -478,22 +581,111 @@ __global__ void __launch_bounds__(C::NT, C::MINB) k_sweep_tiled(const __grid_con
     for (int zr = 0; zr < l[2]; ++zr)
       for (int yr = 0; yr < l[1]; ++yr) {
         const int rb = off + (o[2] + zr) * C::PS + (o[1] + yr) * C::RS + o[0];
-        uint8_t* const grb = gcell + zr * zstr + yr * px;
+        const uint32_t grb = gcell + static_cast<uint32_t>(zr * zstr + yr * g.px);
         const uint32_t cc0 = static_cast<uint32_t>((zr * l[1] + yr) * l[0]);
         for (int xr = 0; xr < l[0]; ++xr) {
           const uint32_t cc = cc0 + xr;
           const int ai = rb + xr;
-          uint8_t* const gi = grb + xr;
+          const uint32_t gi = grb + xr;
+          const uint32_t gs = static_cast<uint32_t>(gstr);
           const U4 w0 = philox4x32_10_rk(cc * (C::NB / 2), cid, a.t, 0u, g.rk);
           attempt(std::integral_constant<int, 0>{}, ai, gi, w0.x, w0.y);
-          attempt(std::integral_constant<int, 1>{}, ai + C::XW, gi + gstr, w0.z, w0.w);
+          attempt(std::integral_constant<int, 1>{}, ai + C::XW, gi + gs, w0.z, w0.w);
           if constexpr (C::NB == 4) {
             const U4 w1 = philox4x32_10_rk(cc * 2 + 1, cid, a.t, 0u, g.rk);
-            attempt(std::integral_constant<int, 2>{}, ai + 2 * C::XW, gi + 2 * gstr, w1.x, w1.y);
-            attempt(std::integral_constant<int, 3>{}, ai + 3 * C::XW, gi + 3 * gstr, w1.z, w1.w);
+            attempt(std::integral_constant<int, 2>{}, ai + 2 * C::XW, gi + 2 * gs, w1.x, w1.y);
+            attempt(std::integral_constant<int, 3>{}, ai + 3 * C::XW, gi + 3 * gs, w1.z, w1.w);
           }
         }
       }
+  }
+
+  // ---- write back --------------------------------------------------------
+  // Tiles whose accepted swaps changed only the tile (packed storage, tiles
+  // across a periodic seam).  The sites a block's trials can have changed
+  // lie within one conventional cell of its link cells (a partner is one
+  // half unit from its anchor): tile indices [1, ext - 1) along every axis,
+  // the cells starting H = 2 in.  No other link cell of this colour writes
+  // there (the edge rule that keeps their interaction zones apart, Sec.
+  // 2.2), so the region is stored whole; its sites that no trial changed get
+  // back the value they already hold.
+  if (!direct) {
+    __syncthreads();
+    const int wy = ext[1] - 2;
+    const int n_wsub = wy * (ext[2] - 2) * C::G;
+    const uint32_t inv_wy = (65536u + wy - 1) / wy;  // exact as inv_ey above
+    auto wsub_row = [=](int sub, int* grp, int* ty, int* tz) {
+      *grp = sub % C::G;
+      const int t = sub / C::G;
+      const int z = static_cast<int>((static_cast<uint32_t>(t) * inv_wy) >> 16);
+      *tz = z + 1;
+      *ty = t - z * wy + 1;
+    };
+    // the stored value of byte t of the sub-row of group grp
+    auto stored = [&](const uint8_t* row, int grp, int t) -> uint32_t {
+      if constexpr (!C::PACK4) {
+        return row[grp * C::XW + t];
+      } else {
+        return code_to_sigma<C::W>(row[(2 * grp) * C::XW + t]) |
+               (code_to_sigma<C::W>(row[(2 * grp + 1) * C::XW + t]) << 4);
+      }
+    };
+    const int a0 = off + 1, a1 = off + ext[0] - 1;  // shared bytes [a0, a1) of a sub-row
+    if (!wrap_x) {
+      // whole 8-byte chunks f0 .. f1-1 of the staging grid (shared offset 8c
+      // <-> global g0x - off + 8c, both 8-byte aligned), spread over every
+      // thread; then the partial chunks at the two ends, byte by byte
+      // (a short tile row may hold one whole chunk or none: nf = 1 divides
+      // exactly without the reciprocal, nf = 0 leaves only the two ends)
+      const int f0 = (a0 + 7) >> 3, f1 = max(a1 >> 3, f0), nf = f1 - f0;
+      const uint32_t inv_nf =
+          nf > 1 ? static_cast<uint32_t>((0x100000000ull + nf - 1) / nf) : 0u;  // exact: jb nf < 2^32
+      uint8_t* const gx0 = occ + (g0[0] - off);
+      for (int jb = tid; jb < n_wsub * nf; jb += C::NT) {
+        const int sub = nf == 1 ? jb : static_cast<int>(__umulhi(static_cast<uint32_t>(jb), inv_nf));
+        const int c = f0 + jb - sub * nf;
+        int grp, ty, tz;
+        wsub_row(sub, &grp, &ty, &tz);
+        const uint8_t* row = tile + tz * C::PS + ty * C::RS + 8 * c;
+        uint2 v;
+        if constexpr (!C::PACK4) {
+          v = *reinterpret_cast<const uint2*>(row + grp * C::XW);
+        } else {
+          const uint2 lo4 = *reinterpret_cast<const uint2*>(row + (2 * grp) * C::XW);
+          const uint2 hi4 = *reinterpret_cast<const uint2*>(row + (2 * grp + 1) * C::XW);
+          v = make_uint2(codes_to_sigma<C::W>(lo4.x) | (codes_to_sigma<C::W>(hi4.x) << 4),
+                         codes_to_sigma<C::W>(lo4.y) | (codes_to_sigma<C::W>(hi4.y) << 4));
+        }
+        *reinterpret_cast<uint2*>(gx0 + grow(grp, ty, tz) + 8 * c) = v;
+      }
+      for (int jb = tid; jb < 2 * n_wsub; jb += C::NT) {
+        const int sub = jb >> 1;
+        // the ends [a0, 8 f0) and [8 f1, a1), clipped to [a0, a1), at most 7
+        // bytes each
+        const int t0 = (jb & 1) ? max(8 * f1, a0) : a0, t1 = (jb & 1) ? a1 : min(8 * f0, a1);
+        int grp, ty, tz;
+        wsub_row(sub, &grp, &ty, &tz);
+        const uint8_t* row = tile + tz * C::PS + ty * C::RS;
+        uint8_t* dst = gx0 + grow(grp, ty, tz);
+#pragma unroll
+        for (int k = 0; k < 7; ++k)
+          if (t0 + k < t1) dst[t0 + k] = static_cast<uint8_t>(stored(row, grp, t0 + k));
+      }
+    } else {
+      // the tile's x range crosses the periodic seam: byte stores, one warp
+      // per sub-row
+      for (int sub = warp; sub < n_wsub; sub += NW) {
+        int grp, ty, tz;
+        wsub_row(sub, &grp, &ty, &tz);
+        uint8_t* dst = occ + grow(grp, ty, tz);
+        const uint8_t* row = tile + tz * C::PS + ty * C::RS;
+        for (int t = a0 + lane; t < a1; t += 32) {
+          int gx = g0[0] + (t - off);
+          gx -= gx >= g.n[0] ? g.n[0] : 0;
+          dst[gx] = static_cast<uint8_t>(stored(row, grp, t));
+        }
+      }
+    }
   }
   warp_reduce_add_stats(stats, n_att, n_unl, n_acc, sum_de);
 }

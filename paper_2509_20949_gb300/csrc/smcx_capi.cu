@@ -209,6 +209,7 @@ struct smcx_lattice {
   smcx_status sticky = SMCX_OK;
   int opt_kernel = 0;
   int opt_tile = -1;
+  int opt_staging = 0;
   int n_sm = 0;
   bool tiled_table_ok = false;  // the tiled kernel's int32 difference table fits
   bool local = false;           // the local-energy model replaces the EPI model
@@ -471,7 +472,7 @@ smcx_status full_energy(smcx_lattice* lat, int64_t* e) {
 // stays an independent check of any later full recompute.  A lattice with no
 // model yet takes its base when the model is set.
 smcx_status restart_running_energy(smcx_lattice* lat) {
-  SMCX_CUDA(lat, cudaMemsetAsync(lat->stats(), 0, sizeof(unsigned long long) * 16, lat->stream));
+  SMCX_CUDA(lat, cudaMemsetAsync(lat->stats(), 0, sizeof(unsigned long long) * 8, lat->stream));
   lat->e0_known = false;
   if (!lat->has_epi) return SMCX_OK;
   int64_t e = 0;
@@ -564,6 +565,7 @@ smcx_status launch_colour_with(smcx_lattice* lat, int colour, const PhaseArgs& b
   TraceRange trace("smcx_colour_phase");
   PhaseArgs a = base;
   a.colour = colour;
+  a.staging = lat->opt_staging;
   const Geom g = lat->geom();
   if (colour_empty(lat, colour)) return SMCX_OK;
   colour_z_range(lat->m, colour, c_lo, c_hi < 0 ? lat->m[2] : c_hi, &a.az0, &a.naz);
@@ -602,11 +604,14 @@ smcx_status launch_colour(smcx_lattice* lat, int colour, const PhaseArgs& base, 
                             c_lo, c_hi);
 }
 
-// Difference rows of the tiled kernel, one per species pair (p, q) at byte
-// (p * KMAX + q) * row_bytes: D'_{m,s} = D_{m,s} - D_{m,0} (int32) for
-// s = 1..K-1 with D_{m,s} = V_m(q,s) - V_m(p,s), then the int64 constant
-// C = [32 sum_{m,s} D'_{m,s} when K <= 5] + D_{1,q} - D_{1,p}.  Returns false
-// when a D' does not fit int32.
+// Difference rows of the tiled and cell kernels, one per species pair (p, q)
+// at byte (p * kmax + q) * row_bytes, with D_{m,s} = V_m(q,s) - V_m(p,s) and
+// the i-j bond term B = (V_1(q,q) - V_1(p,q)) - (V_1(q,p) - V_1(p,p)):
+//   K <= 5 (kmax 5): D'_{m,s} = D_{m,s} - D_{m,4} (D_{m,4} = 0 when K < 5) for
+//     s = 0..3, stored per shell m as four words, word t holding byte t of
+//     D'_{m,0}, .., D'_{m,3}; then the int64 C = 128 sum_{m,s} D'_{m,s} + B;
+//   K = 6 (kmax 6): int32 D'_{m,s} = D_{m,s} - D_{m,0} for s = 1..5, then C = B.
+// Returns false when a D' does not fit int32.
 bool dtable_of(const smcx_lattice_desc& d, int M, const int64_t* Vt, std::vector<uint8_t>* bytes,
                int* kmax_out) {
   const int K = static_cast<int>(d.n_species);
@@ -621,13 +626,25 @@ bool dtable_of(const smcx_lattice_desc& d, int M, const int64_t* Vt, std::vector
       uint8_t* row = bytes->data() + static_cast<size_t>(p * kmax + q) * rowb;
       __int128 C = 0;
       for (int m = 0; m < M; ++m) {
-        const int64_t d0 = V(m, q, 0) - V(m, p, 0);
-        for (int s = 1; s < K; ++s) {
-          const int64_t dp = (V(m, q, s) - V(m, p, s)) - d0;
-          if (dp > INT32_MAX || dp < INT32_MIN) return false;
-          const int32_t v32 = static_cast<int32_t>(dp);
-          std::memcpy(row + 4 * (m * (kmax - 1) + s - 1), &v32, 4);
-          if (kmax == 5) C += static_cast<__int128>(32) * dp;
+        if (kmax == 5) {
+          const int64_t d4 = K == 5 ? V(m, q, 4) - V(m, p, 4) : 0;
+          uint32_t w[4] = {0, 0, 0, 0};
+          for (int s = 0; s < 4; ++s) {
+            const int64_t dp = s < K ? (V(m, q, s) - V(m, p, s)) - d4 : -d4;
+            if (dp > INT32_MAX || dp < INT32_MIN) return false;
+            const uint32_t u = static_cast<uint32_t>(static_cast<int32_t>(dp));
+            for (int t = 0; t < 4; ++t) w[t] |= ((u >> (8 * t)) & 0xFFu) << (8 * s);
+            C += static_cast<__int128>(128) * dp;
+          }
+          std::memcpy(row + 16 * m, w, 16);
+        } else {
+          const int64_t d0 = V(m, q, 0) - V(m, p, 0);
+          for (int s = 1; s < K; ++s) {
+            const int64_t dp = (V(m, q, s) - V(m, p, s)) - d0;
+            if (dp > INT32_MAX || dp < INT32_MIN) return false;
+            const int32_t v32 = static_cast<int32_t>(dp);
+            std::memcpy(row + 4 * (m * (kmax - 1) + s - 1), &v32, 4);
+          }
         }
       }
       C += (V(0, q, q) - V(0, p, q)) - (V(0, q, p) - V(0, p, p));
@@ -650,10 +667,15 @@ bool build_tiled_table(smcx_lattice* lat, std::vector<uint32_t>* out) {
 }
 
 smcx_status read_call_stats(smcx_lattice* lat, smcx_sweep_stats* out) {
-  unsigned long long h[4];
+  unsigned long long h[kStatWait + 1];
   SMCX_CUDA(lat, cudaMemcpyAsync(h, lat->stats() + kStatCall, sizeof(h), cudaMemcpyDeviceToHost,
                                  lat->stream));
   SMCX_CUDA(lat, cudaStreamSynchronize(lat->stream));
+  if (h[kStatWait] != 0) {
+    SMCX_CUDA(lat, cudaMemsetAsync(lat->stats() + kStatWait, 0, sizeof(unsigned long long),
+                                   lat->stream));
+    return fail(SMCX_ETIMEOUT, "a staging wait of the tiled sweep gave up");
+  }
   out->attempts = h[0];
   out->unlike = h[1];
   out->accepted = h[2];
@@ -729,6 +751,11 @@ smcx_status smcx_create_lattice(const smcx_lattice_desc* desc, void* d_occ, void
   if (e != cudaSuccess) {
     delete lat;
     return fail(SMCX_ECUDA, std::string("device query: ") + cudaGetErrorString(e));
+  }
+  if (cudaMemsetAsync(lat->stats(), 0, sizeof(unsigned long long) * 16, lat->stream) !=
+      cudaSuccess) {
+    delete lat;
+    return fail(SMCX_ECUDA, "workspace clear failed");
   }
   s = upload_occupancy(lat, h_init);
   if (s == SMCX_OK) s = restart_running_energy(lat);
@@ -1311,7 +1338,7 @@ smcx_status smcx_restore(smcx_lattice* lat, const void* buf, size_t len) {
   }
   s = upload_occupancy(lat, occ);
   if (s != SMCX_OK) return s;
-  SMCX_CUDA(lat, cudaMemsetAsync(lat->stats(), 0, sizeof(unsigned long long) * 16, lat->stream));
+  SMCX_CUDA(lat, cudaMemsetAsync(lat->stats(), 0, sizeof(unsigned long long) * 8, lat->stream));
   SMCX_CUDA(lat, cudaStreamSynchronize(lat->stream));
   lat->E0 = e_run;
   lat->e0_known = true;
@@ -1331,6 +1358,12 @@ smcx_status smcx_set_option(smcx_lattice* lat, uint32_t key, int64_t value) {
     if (value < -1 || value >= static_cast<int64_t>(smcx_tile_shape_count(lat->desc.kind)))
       return fail(SMCX_EINVAL, "tile shape index out of range");
     lat->opt_tile = static_cast<int>(value);
+    tuning_reset(lat);
+    return SMCX_OK;
+  }
+  if (key == SMCX_OPT_STAGING) {
+    if (value < 0 || value > 1) return fail(SMCX_EINVAL, "staging option must be 0 or 1");
+    lat->opt_staging = static_cast<int>(value);
     tuning_reset(lat);
     return SMCX_OK;
   }

@@ -134,8 +134,9 @@ __host__ __device__ __forceinline__ uint32_t compose_threshold(uint32_t t0, uint
 // canonical layout).  Rows of px bytes (n_x rounded up to 16) ordered
 // [group][z][y]:
 //   8-bit: group = basis site b, byte x holds the code sigma * W of site
-//          (x, y, z, b) -- W is the field width of the one-hot species
-//          counters of the tiled sweep (6 for K <= 5, 5 for K = 6, 1 above);
+//          (x, y, z, b) -- W is the bit position step of the one-hot species
+//          counters of the tiled and cell sweeps (8 for K <= 5: species s
+//          counted in byte s, species 4 shifted out; 5 for K = 6; 1 above);
 //   4-bit: group = basis pair b/2, byte x holds sigma of b even in the low
 //          and of b odd in the high nibble (both sites of one conventional
 //          cell, so no two link cells ever write one byte).
@@ -183,7 +184,7 @@ __host__ __device__ __forceinline__ U4 philox4x32_10_rk(uint32_t c0, uint32_t c1
   return U4{c0, c1, c2, c3};
 }
 
-__host__ __device__ inline int code_width(int K) { return K <= 5 ? 6 : (K == 6 ? 5 : 1); }
+__host__ __device__ inline int code_width(int K) { return K <= 5 ? 8 : (K == 6 ? 5 : 1); }
 
 __host__ __device__ inline size_t dev_row(const Geom& g, int grp, int z, int y) {
   return ((static_cast<size_t>(grp) * g.n[2] + z) * g.n[1] + y) * static_cast<size_t>(g.px);
@@ -198,6 +199,7 @@ struct PhaseArgs {
   // of the cells c_z = 2 a + (colour >> 2 & 1) (all of them unless a run is
   // restricted to a range of z planes of cells)
   int az0, naz;
+  int staging;     // tiled kernel: 0 = bulk copies where they fit, 1 = 8-byte copies only
 };
 
 struct Tables {
@@ -205,10 +207,13 @@ struct Tables {
 };
 
 // Device-side statistics block inside the workspace: [0..3] this call,
-// [4..7] since the running energy was last (re)started, [8] error status.
+// [4..7] since the running energy was last (re)started, [8] upload
+// validation flag, [9] set when a device wait of a sweep kernel gave up
+// (sticky until the host reads it).
 constexpr int kStatCall = 0;
 constexpr int kStatCum = 4;
 constexpr int kStatStatus = 8;
+constexpr int kStatWait = 9;
 
 // Shell vectors of one lattice kind for device lookups (generic kernels).
 struct ShellParam {

@@ -29,11 +29,12 @@ static cudaError_t dispatch(int shape, const Geom& g, const PhaseArgs& a, const 
 }
 }  // namespace tiled
 
-static const int kShapeCells[2][2][3] = {{{16, 2, 8}, {16, 2, 4}}, {{16, 2, 4}, {16, 2, 2}}};
+static const int kShapeCells[2][3][3] = {{{16, 2, 8}, {16, 2, 4}, {32, 1, 8}},
+                                         {{16, 2, 4}, {16, 2, 2}, {32, 1, 4}}};
 
 int tiled_shape_count(int kind) {
   (void)kind;
-  return 2;
+  return 3;
 }
 
 void tiled_shape_cells(int kind, int shape, int cells[3]) {

@@ -13,11 +13,13 @@ pytestmark = pytest.mark.gpu
 GENERIC, TILED = 1, 2
 
 
-def _compare_sweeps(orc, case, sweeps, T, pack_bits=8, shape=None):
+def _compare_sweeps(orc, case, sweeps, T, pack_bits=8, shape=None, staging=None):
     require_cuda()
     lat = gpu_lattice(case, pack_bits=pack_bits, kernel=TILED)
     if shape is not None:
         lat.set_option(2, shape)
+    if staging is not None:
+        lat.set_option(3, staging)
     kern, sh = lat.kernel_in_use()
     assert kern == TILED
     d = oracle_desc(orc, case)
@@ -61,6 +63,37 @@ def test_tiled_shapes_and_packing(orc, pack, shape):
     _compare_sweeps(orc, case, 2, 900.0, pack_bits=pack, shape=shape)
     case = make_case(1, (68, 13, 20), 4, 4, seed=5, sigma=0.02)
     _compare_sweeps(orc, case, 2, 700.0, pack_bits=pack, shape=shape)
+
+
+@pytest.mark.parametrize("pack", [8, 4])
+@pytest.mark.parametrize("staging", [0, 1])
+def test_tiled_staging_paths(orc, pack, staging):
+    """Tiles filled by bulk (TMA) copies of each row's 16-byte aligned span
+    (staging 0, wherever it fits; 8-byte cp.async copies elsewhere) and by
+    8-byte copies only (staging 1): eight sweeps each, so the per-sweep origin
+    shifts put the tile rows at many alignments, including tiles across the
+    periodic seams; uniform and ragged x edges."""
+    case = make_case(0, (68, 12, 36), 5, 3, seed=31, sigma=0.02)    # uniform edges
+    _compare_sweeps(orc, case, 8, 1000.0, pack_bits=pack, staging=staging)
+    case = make_case(1, (68, 13, 21), 4, 3, seed=32, sigma=0.02)    # FCC, ragged y and z
+    _compare_sweeps(orc, case, 8, 900.0, pack_bits=pack, staging=staging)
+    case = make_case(0, (71, 12, 20), 5, 2, seed=33, sigma=0.03)    # ragged x: copies only
+    _compare_sweeps(orc, case, 4, 1300.0, pack_bits=pack, staging=staging)
+
+
+@pytest.mark.parametrize("pack", [8, 4])
+def test_tiled_wide_warp_shape(orc, pack):
+    """Tile shape 2: warps of 32 link cells along x (a tile needs one more
+    active cell than it holds along each axis: BCC 32 x 1 x 8, FCC 32 x 1 x
+    4): uniform and ragged edges, BCC and FCC, both storages."""
+    case = make_case(0, (136, 8, 36), 5, 3, seed=21, sigma=0.02)    # uniform edges
+    _compare_sweeps(orc, case, 2, 1150.0, pack_bits=pack, shape=2)
+    case = make_case(0, (139, 11, 39), 4, 2, seed=22, sigma=0.03)   # ragged in every dimension
+    _compare_sweeps(orc, case, 2, 800.0, pack_bits=pack, shape=2)
+    case = make_case(1, (137, 9, 21), 5, 3, seed=23, sigma=0.02)    # FCC, ragged
+    _compare_sweeps(orc, case, 2, 1000.0, pack_bits=pack, shape=2)
+    case = make_case(0, (136, 10, 38), 6, 3, seed=24, sigma=0.02)   # K = 6
+    _compare_sweeps(orc, case, 2, 600.0, pack_bits=pack, shape=2)
 
 
 @pytest.mark.parametrize("T", [0.0, float("inf"), 100.0])
