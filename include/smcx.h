@@ -380,9 +380,11 @@ const char* smcx_last_error(void);
    temperature.
 
    Memory: the caller provides one device arena (256-byte aligned); its first
-   smcx_batch_control_bytes(max_jobs, transfer_bytes) bytes hold tables and a
-   transfer buffer of transfer_bytes (>= the largest job's site count), the
-   rest is the job heap.  No other device memory is used. */
+   smcx_batch_control_bytes(max_jobs, transfer_bytes) bytes hold tables and
+   two transfer buffers of transfer_bytes (>= the largest job's site count;
+   the second serves admissions and read-backs while a chunk runs), the rest
+   is the job heap.  No other device memory is used; the batch creates one
+   side stream of its own and an 8-byte pinned host word. */
 typedef struct smcx_batch smcx_batch;
 
 /* Bytes of the arena's control area; 0 for max_jobs == 0. */
@@ -399,10 +401,13 @@ smcx_status smcx_batch_create(uint32_t max_jobs, void* d_arena, size_t arena_byt
 
 /* Admits a job: occupancy h_init (canonical, N bytes), EPI [n_shells][K][K]
    (q units, symmetric), temperature T (kelvin, constant), n_sweeps to run.
-   The job starts at sweep counter 0 and joins the next smcx_batch_run.
-   *job_id receives its id (a slot index, reused after smcx_batch_remove).
-   EBUDGET: no free slot or no room left in the arena.  EINVAL: invalid or
-   unsupported job. */
+   The job starts at sweep counter 0 and joins the next chunk
+   (smcx_batch_run or smcx_batch_launch).  While a launched chunk runs, the
+   upload and the job's initial energy go through the batch's side stream
+   and a second transfer buffer, overlapping the chunk on the device (the
+   call still returns only when the job is admitted).  *job_id receives its
+   id (a slot index, reused after smcx_batch_remove).  EBUDGET: no free slot
+   or no room left in the arena.  EINVAL: invalid or unsupported job. */
 smcx_status smcx_batch_add(smcx_batch* b, const smcx_lattice_desc* desc, const uint8_t* h_init,
                            uint32_t n_shells, const int64_t* v_q, double T, uint32_t n_sweeps,
                            uint32_t* job_id);
@@ -414,6 +419,22 @@ smcx_status smcx_batch_add(smcx_batch* b, const smcx_lattice_desc* desc, const u
    tuning candidate (results are unaffected).  ETIMEOUT: a device-side wait
    gave up (the batch then stays in an error state). */
 smcx_status smcx_batch_run(smcx_batch* b, uint32_t chunk_sweeps, uint32_t* n_finished);
+
+/* The same chunk split in two, so that host work overlaps the device:
+   smcx_batch_launch enqueues up to chunk_sweeps sweeps of every active job
+   on the batch's stream and returns at once (first completing a chunk still
+   in flight); smcx_batch_wait completes the chunk in flight and *n_finished
+   (may be NULL) receives the number of jobs finished since the last report.
+   Results are those of smcx_batch_run.  Between the two calls,
+   smcx_batch_add admits jobs for the next chunk and smcx_batch_result /
+   smcx_batch_remove serve jobs that finished earlier, through the side
+   stream; smcx_batch_poll reports jobs finished by completed chunks only.
+   Calls that need the running jobs (their results, exchange, queue
+   statistics, smcx_batch_run) complete the chunk first.  While the batch is
+   still tuning, smcx_batch_launch runs its chunk to completion (the tuning
+   times it).  ETIMEOUT as for smcx_batch_run. */
+smcx_status smcx_batch_launch(smcx_batch* b, uint32_t chunk_sweeps);
+smcx_status smcx_batch_wait(smcx_batch* b, uint32_t* n_finished);
 
 /* Tuning of the batched sweep (never changes results):
      SMCX_BATCH_OPT_TILE       work-item shape index (see smcx_batch_tile_shape)

@@ -178,6 +178,8 @@ SIGNATURES = {
     "smcx_batch_add": (_st, [_vp, _P(LatticeDesc), _vp, ctypes.c_uint32, _vp, ctypes.c_double,
                              ctypes.c_uint32, _P(ctypes.c_uint32)]),
     "smcx_batch_run": (_st, [_vp, ctypes.c_uint32, _P(ctypes.c_uint32)]),
+    "smcx_batch_launch": (_st, [_vp, ctypes.c_uint32]),
+    "smcx_batch_wait": (_st, [_vp, _P(ctypes.c_uint32)]),
     "smcx_batch_poll": (_st, [_vp, _P(ctypes.c_uint32), ctypes.c_uint32, _P(ctypes.c_uint32)]),
     "smcx_batch_result": (_st, [_vp, ctypes.c_uint32, _vp, _P(SweepStats), _P(ctypes.c_int64),
                                 _P(ctypes.c_uint32)]),

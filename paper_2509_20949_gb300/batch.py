@@ -84,6 +84,18 @@ class Batch:
         check(self.L.smcx_batch_run(self.h, int(chunk_sweeps), ctypes.byref(fin)))
         return int(fin.value)
 
+    def launch(self, chunk_sweeps: int):
+        """Enqueues one chunk for every active job and returns at once
+        (smcx_batch_launch); wait() completes it."""
+        check(self.L.smcx_batch_launch(self.h, int(chunk_sweeps)))
+
+    def wait(self) -> int:
+        """Completes the launched chunk; the number of jobs finished since the
+        last report (smcx_batch_wait)."""
+        fin = ctypes.c_uint32()
+        check(self.L.smcx_batch_wait(self.h, ctypes.byref(fin)))
+        return int(fin.value)
+
     def poll(self, cap: int = 4096):
         ids = (ctypes.c_uint32 * cap)()
         n = ctypes.c_uint32()

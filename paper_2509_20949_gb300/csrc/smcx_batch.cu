@@ -142,7 +142,9 @@ struct Job {
 };
 
 struct ControlLayout {
-  size_t jobs, tabs, dtabs, stats, order, first, ctr, qstats, pairs, flag, scratch, heap;
+  size_t jobs, tabs, dtabs, stats, order, first, ctr, qstats, pairs, flag, scratch;
+  size_t pairs2, flag2, scratch2;  // the side stream's (admission and results during a chunk)
+  size_t heap;
 };
 
 ControlLayout control_layout(uint32_t max_jobs, size_t transfer_bytes) {
@@ -169,6 +171,12 @@ ControlLayout control_layout(uint32_t max_jobs, size_t transfer_bytes) {
   c.flag = o;
   o += kAlign;
   c.scratch = o;
+  o += aup(transfer_bytes, kAlign);
+  c.pairs2 = o;
+  o += aup(sizeof(unsigned long long) * 4 * 6 * 6, kAlign);
+  c.flag2 = o;
+  o += kAlign;
+  c.scratch2 = o;
   o += aup(transfer_bytes, kAlign);
   c.heap = o;
   return c;
@@ -269,6 +277,18 @@ struct smcx_batch {
   cudaGraphExec_t graph = nullptr;
   uint32_t graph_sweeps = 0;
   int graph_tile = -1, graph_sched = -1, graph_occ = -1;
+  // a chunk launched by smcx_batch_launch and not yet completed: its sweeps,
+  // the jobs it runs, the event after its status read-back, the status word
+  // (pinned host memory) and the jobs finished by chunks already completed
+  // but not yet reported by smcx_batch_wait
+  bool in_flight = false;
+  uint32_t flight_sweeps = 0;
+  std::vector<uint32_t> flight_jobs;
+  cudaEvent_t ev_chunk = nullptr;
+  unsigned long long* h_status = nullptr;
+  uint32_t unreported_fin = 0;
+  // side stream: admission and result read-back while a chunk runs
+  cudaStream_t side = nullptr;
 
   uint8_t* at(size_t off) { return arena + off; }
   uint8_t* scratch() { return at(cl.scratch); }
@@ -380,11 +400,32 @@ smcx_status enqueue_chunk(smcx_batch* b, uint32_t sweeps, int tile, int sched, i
   return SMCX_OK;
 }
 
+// Advances the listed jobs by one completed chunk of `sweeps` sweeps and
+// queues those that finished; returns how many finished.
+uint32_t advance_jobs(smcx_batch* b, const std::vector<uint32_t>& slots, uint32_t sweeps) {
+  uint32_t fin = 0;
+  for (uint32_t slot : slots) {
+    Job& j = b->jobs[slot];
+    const uint32_t ran = std::min(sweeps, j.total - j.done_sweeps);
+    j.done_sweeps += ran;
+    j.t += ran;
+    if (j.done_sweeps == j.total) {
+      j.done = true;
+      b->done_queue.push_back(slot);
+      b->dirty = true;
+      ++fin;
+    }
+  }
+  return fin;
+}
+
 // Runs `sweeps` sweeps of every active job with (tile, sched, occ);
 // graph-captured when `use_graph` and a stream is bound.  *trials =
 // attempted swaps, *ms = device time (when ms != NULL, timed with events).
+// async: enqueue only; complete_chunk finishes it.
 smcx_status run_sweeps(smcx_batch* b, uint32_t sweeps, int tile, int sched, int occ,
-                       bool use_graph, uint32_t* n_finished, uint64_t* trials, float* ms) {
+                       bool use_graph, uint32_t* n_finished, uint64_t* trials, float* ms,
+                       bool async = false) {
   TraceRange trace(sched == 0 ? "smcx_batch_chunk_queue" : "smcx_batch_chunk_phases");
   smcx_status s;
   if (b->dirty || b->queue_tile != tile) {
@@ -455,6 +496,17 @@ smcx_status run_sweeps(smcx_batch* b, uint32_t sweeps, int tile, int sched, int 
     if (s != SMCX_OK) return s;
   }
   if (ms) BATCH_CUDA(b, cudaEventRecord(b->ev[1], b->stream));
+  if (async) {
+    // the status word comes back with the chunk; smcx_batch_wait reads it
+    // and advances the jobs
+    BATCH_CUDA(b, cudaMemcpyAsync(b->h_status, b->ctr() + 1, sizeof(unsigned long long),
+                                  cudaMemcpyDeviceToHost, b->stream));
+    BATCH_CUDA(b, cudaEventRecord(b->ev_chunk, b->stream));
+    b->in_flight = true;
+    b->flight_sweeps = sweeps;
+    b->flight_jobs = b->order;
+    return SMCX_OK;
+  }
   unsigned long long status = 0;
   BATCH_CUDA(b, cudaMemcpyAsync(&status, b->ctr() + 1, sizeof(status), cudaMemcpyDeviceToHost,
                                 b->stream));
@@ -464,35 +516,39 @@ smcx_status run_sweeps(smcx_batch* b, uint32_t sweeps, int tile, int sched, int 
     return batch_fail(SMCX_ETIMEOUT, "batched sweep: a wait for a job's previous phase gave up");
   }
   if (ms) BATCH_CUDA(b, cudaEventElapsedTime(ms, b->ev[0], b->ev[1]));
-  uint32_t fin = 0;
-  for (uint32_t slot : b->order) {
-    Job& j = b->jobs[slot];
-    const uint32_t ran = std::min(sweeps, j.total - j.done_sweeps);
-    j.done_sweeps += ran;
-    j.t += ran;
-    if (j.done_sweeps == j.total) {
-      j.done = true;
-      b->done_queue.push_back(slot);
-      b->dirty = true;
-      ++fin;
-    }
-  }
+  const uint32_t fin = advance_jobs(b, b->order, sweeps);
   if (n_finished) *n_finished = fin;
   return SMCX_OK;
 }
 
-smcx_status job_energy(smcx_batch* b, Job& j, int64_t* e) {
+// Completes the chunk in flight (if any): waits for it, checks its status
+// and advances its jobs; the jobs it finished are counted for the next
+// smcx_batch_wait.
+smcx_status complete_chunk(smcx_batch* b) {
+  if (!b->in_flight) return SMCX_OK;
+  b->in_flight = false;
+  BATCH_CUDA(b, cudaEventSynchronize(b->ev_chunk));
+  if (*b->h_status != 0) {
+    b->sticky = SMCX_ETIMEOUT;
+    return batch_fail(SMCX_ETIMEOUT, "batched sweep: a wait for a job's previous phase gave up");
+  }
+  b->unreported_fin += advance_jobs(b, b->flight_jobs, b->flight_sweeps);
+  b->flight_jobs.clear();
+  return SMCX_OK;
+}
+
+smcx_status job_energy(smcx_batch* b, Job& j, int64_t* e, cudaStream_t st, size_t pairs_off) {
   const Geom& g = j.g;
   const size_t kmax = g.K <= 5 ? 5 : 6;
   const size_t n_h = static_cast<size_t>(j.M) * kmax * kmax;
-  unsigned long long* d_pairs = reinterpret_cast<unsigned long long*>(b->at(b->cl.pairs));
-  BATCH_CUDA(b, cudaMemsetAsync(d_pairs, 0, sizeof(uint64_t) * n_h, b->stream));
+  unsigned long long* d_pairs = reinterpret_cast<unsigned long long*>(b->at(pairs_off));
+  BATCH_CUDA(b, cudaMemsetAsync(d_pairs, 0, sizeof(uint64_t) * n_h, st));
   BATCH_CUDA(b, launch_pair_count_tiled(g, static_cast<int>(j.M), b->at(j.occ_off), d_pairs,
-                                        b->n_sm, b->stream, false));
+                                        b->n_sm, st, false));
   std::vector<uint64_t> h(n_h);
   BATCH_CUDA(b, cudaMemcpyAsync(h.data(), d_pairs, sizeof(uint64_t) * n_h, cudaMemcpyDeviceToHost,
-                                b->stream));
-  BATCH_CUDA(b, cudaStreamSynchronize(b->stream));
+                                st));
+  BATCH_CUDA(b, cudaStreamSynchronize(st));
   const size_t K = g.K;
   __int128 acc = 0;
   for (size_t m = 0; m < j.M; ++m)
@@ -559,9 +615,16 @@ smcx_status smcx_batch_create(uint32_t max_jobs, void* d_arena, size_t arena_byt
   }
   if (e == cudaSuccess) e = cudaEventCreate(&b->ev[0]);
   if (e == cudaSuccess) e = cudaEventCreate(&b->ev[1]);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_chunk, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->side, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaHostAlloc(reinterpret_cast<void**>(&b->h_status),
+                                          sizeof(unsigned long long), cudaHostAllocDefault);
   if (e != cudaSuccess) {
     for (cudaEvent_t ev : b->ev)
       if (ev) cudaEventDestroy(ev);
+    if (b->ev_chunk) cudaEventDestroy(b->ev_chunk);
+    if (b->side) cudaStreamDestroy(b->side);
+    if (b->h_status) cudaFreeHost(b->h_status);
     delete b;
     return batch_fail(SMCX_ECUDA, std::string("batch create: ") + cudaGetErrorString(e));
   }
@@ -625,29 +688,33 @@ smcx_status smcx_batch_add(smcx_batch* b, const smcx_lattice_desc* desc, const u
     b->heap.release(off, ob);
     return st;
   };
-  // upload: canonical -> transfer buffer -> validated -> device layout
-  cudaError_t e = cudaMemcpyAsync(b->scratch(), h_init, N, cudaMemcpyHostToDevice, b->stream);
-  if (e == cudaSuccess) e = cudaMemsetAsync(b->flag(), 0, sizeof(unsigned int), b->stream);
-  if (e == cudaSuccess)
-    e = launch_validate(b->scratch(), N, desc->n_species, b->flag(), b->n_sm, b->stream);
+  // upload: canonical -> transfer buffer -> validated -> device layout.
+  // While a chunk runs this goes through the side stream and its own
+  // transfer buffer, flag and pair counts: the new job's heap block and slot
+  // are not in the running chunk, so the two overlap on the device.
+  const bool side = b->in_flight;
+  cudaStream_t st = side ? b->side : b->stream;
+  uint8_t* scr = b->at(side ? b->cl.scratch2 : b->cl.scratch);
+  unsigned int* flg = reinterpret_cast<unsigned int*>(b->at(side ? b->cl.flag2 : b->cl.flag));
+  cudaError_t e = cudaMemcpyAsync(scr, h_init, N, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(flg, 0, sizeof(unsigned int), st);
+  if (e == cudaSuccess) e = launch_validate(scr, N, desc->n_species, flg, b->n_sm, st);
   unsigned int bad = 0;
-  if (e == cudaSuccess)
-    e = cudaMemcpyAsync(&bad, b->flag(), sizeof(bad), cudaMemcpyDeviceToHost, b->stream);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&bad, flg, sizeof(bad), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) return fail_release(bcuda(b, e, "batch upload"));
   if (bad) return fail_release(batch_fail(SMCX_EINVAL, "species id >= n_species in occupancy"));
-  e = launch_canon_to_dev(j.g, b->scratch(), b->at(j.occ_off), static_cast<uint32_t>(N / j.g.nb),
-                            b->n_sm, b->stream);
+  e = launch_canon_to_dev(j.g, scr, b->at(j.occ_off), static_cast<uint32_t>(N / j.g.nb), b->n_sm,
+                          st);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(b->at(b->cl.tabs) + kTabBytes * slot, tab.w, kTabBytes,
-                        cudaMemcpyHostToDevice, b->stream);
+                        cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(b->at(b->cl.dtabs) + kDtabBytes * slot, dtab.data(), dtab.size(),
-                        cudaMemcpyHostToDevice, b->stream);
-  if (e == cudaSuccess)
-    e = cudaMemsetAsync(b->stats(slot), 0, sizeof(unsigned long long) * 8, b->stream);
+                        cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(b->stats(slot), 0, sizeof(unsigned long long) * 8, st);
   if (e != cudaSuccess) return fail_release(bcuda(b, e, "batch add"));
-  s = job_energy(b, j, &j.E0);
+  s = job_energy(b, j, &j.E0, st, side ? b->cl.pairs2 : b->cl.pairs);
   if (s != SMCX_OK) return fail_release(s);
   b->jobs[slot] = j;
   if (n_sweeps == 0) {
@@ -664,6 +731,10 @@ smcx_status smcx_batch_run(smcx_batch* b, uint32_t chunk_sweeps, uint32_t* n_fin
   if (s != SMCX_OK) return s;
   if (chunk_sweeps == 0) return batch_fail(SMCX_EINVAL, "chunk_sweeps must be > 0");
   if (n_finished) *n_finished = 0;
+  s = complete_chunk(b);
+  if (s != SMCX_OK) return s;
+  if (n_finished) *n_finished = b->unreported_fin;
+  b->unreported_fin = 0;
   uint32_t left = chunk_sweeps;
   while (left > 0) {
     if (b->dirty) {
@@ -700,6 +771,45 @@ smcx_status smcx_batch_run(smcx_batch* b, uint32_t chunk_sweeps, uint32_t* n_fin
     }
     if (n_finished) *n_finished += fin;
   }
+  return SMCX_OK;
+}
+
+smcx_status smcx_batch_launch(smcx_batch* b, uint32_t chunk_sweeps) {
+  smcx_status s = bcheck(b);
+  if (s != SMCX_OK) return s;
+  if (chunk_sweeps == 0) return batch_fail(SMCX_EINVAL, "chunk_sweeps must be > 0");
+  s = complete_chunk(b);
+  if (s != SMCX_OK) return s;
+  // the jobs admitted through the side stream are on the device
+  if (b->side) BATCH_CUDA(b, cudaStreamSynchronize(b->side));
+  bool retune = false;
+  if (b->dirty && b->tuner.tuned) {
+    uint64_t items = 0;
+    for (const Job& j : b->jobs)
+      if (j.used && !j.done) items += job_items(j, b->tuner.best[0], nullptr, nullptr);
+    const uint64_t ref = b->tuner.tuned_items;
+    retune = items > 0 && (items > 2 * ref || 2 * items < ref);
+  }
+  if (!b->tuner.tuned || retune || !b->stream) {
+    // tuning times its candidates, which needs the chunk finished: run it
+    // here (the finished jobs are reported by the next smcx_batch_wait)
+    uint32_t fin = 0;
+    s = smcx_batch_run(b, chunk_sweeps, &fin);
+    b->unreported_fin += fin;
+    return s;
+  }
+  uint64_t trials = 0;
+  return run_sweeps(b, chunk_sweeps, b->tuner.tile(), b->tuner.sched(), b->tuner.occ(), true,
+                    nullptr, &trials, nullptr, true);
+}
+
+smcx_status smcx_batch_wait(smcx_batch* b, uint32_t* n_finished) {
+  smcx_status s = bcheck(b);
+  if (s != SMCX_OK) return s;
+  s = complete_chunk(b);
+  if (s != SMCX_OK) return s;
+  if (n_finished) *n_finished = b->unreported_fin;
+  b->unreported_fin = 0;
   return SMCX_OK;
 }
 
@@ -746,6 +856,8 @@ smcx_status smcx_batch_exchange(smcx_batch* b, uint32_t* ladder, uint32_t n, uin
                                 uint32_t round, uint32_t* n_accepted) {
   TraceRange trace("smcx_batch_exchange");
   smcx_status s = bcheck(b);
+  if (s != SMCX_OK) return s;
+  s = complete_chunk(b);  // the energies and tables belong to completed sweeps
   if (s != SMCX_OK) return s;
   if (!ladder || n < 2) return batch_fail(SMCX_EINVAL, "exchange needs a ladder of >= 2 jobs");
   std::vector<bool> seen(b->max_jobs, false);
@@ -811,6 +923,8 @@ smcx_status smcx_batch_temperature(smcx_batch* b, uint32_t job_id, double* T) {
 smcx_status smcx_batch_queue_stats(smcx_batch* b, uint64_t* out) {
   smcx_status s = bcheck(b);
   if (s != SMCX_OK) return s;
+  s = complete_chunk(b);
+  if (s != SMCX_OK) return s;
   if (!out) return batch_fail(SMCX_EINVAL, "null output");
   unsigned long long h[3];
   BATCH_CUDA(b, cudaMemcpyAsync(h, b->qstats(), sizeof(h), cudaMemcpyDeviceToHost, b->stream));
@@ -850,15 +964,24 @@ smcx_status smcx_batch_result(smcx_batch* b, uint32_t job_id, uint8_t* h_occ,
   if (s != SMCX_OK) return s;
   if (job_id >= b->max_jobs || !b->jobs[job_id].used) return batch_fail(SMCX_EINVAL, "unknown job");
   Job& j = b->jobs[job_id];
+  if (!j.done) {  // its occupancy and statistics may be those of a running chunk
+    s = complete_chunk(b);
+    if (s != SMCX_OK) return s;
+  }
+  // a finished job is in no chunk: while one runs, read it back through the
+  // side stream and its own transfer buffer
+  const bool side = b->in_flight;
+  cudaStream_t rs = side ? b->side : b->stream;
+  uint8_t* scr = b->at(side ? b->cl.scratch2 : b->cl.scratch);
   if (h_occ) {
     const uint64_t N = static_cast<uint64_t>(j.g.nb) * j.g.n[0] * j.g.n[1] * j.g.n[2];
-    BATCH_CUDA(b, launch_dev_to_canon(j.g, b->at(j.occ_off), b->scratch(),
-                                      static_cast<uint32_t>(N / j.g.nb), b->n_sm, b->stream));
-    BATCH_CUDA(b, cudaMemcpyAsync(h_occ, b->scratch(), N, cudaMemcpyDeviceToHost, b->stream));
+    BATCH_CUDA(b, launch_dev_to_canon(j.g, b->at(j.occ_off), scr, static_cast<uint32_t>(N / j.g.nb),
+                                      b->n_sm, rs));
+    BATCH_CUDA(b, cudaMemcpyAsync(h_occ, scr, N, cudaMemcpyDeviceToHost, rs));
   }
   unsigned long long st[8];
-  BATCH_CUDA(b, cudaMemcpyAsync(st, b->stats(job_id), sizeof(st), cudaMemcpyDeviceToHost, b->stream));
-  BATCH_CUDA(b, cudaStreamSynchronize(b->stream));
+  BATCH_CUDA(b, cudaMemcpyAsync(st, b->stats(job_id), sizeof(st), cudaMemcpyDeviceToHost, rs));
+  BATCH_CUDA(b, cudaStreamSynchronize(rs));
   if (totals) {
     totals->attempts = st[4];
     totals->unlike = st[5];
@@ -875,6 +998,10 @@ smcx_status smcx_batch_remove(smcx_batch* b, uint32_t job_id) {
   if (s != SMCX_OK) return s;
   if (job_id >= b->max_jobs || !b->jobs[job_id].used) return batch_fail(SMCX_EINVAL, "unknown job");
   Job& j = b->jobs[job_id];
+  if (!j.done) {  // a job of the running chunk
+    s = complete_chunk(b);
+    if (s != SMCX_OK) return s;
+  }
   b->heap.release(j.occ_off - b->cl.heap, j.occ_bytes);
   j = Job();
   b->done_queue.erase(std::remove(b->done_queue.begin(), b->done_queue.end(), job_id),
@@ -900,9 +1027,14 @@ smcx_status smcx_batch_info(smcx_batch* b, uint32_t* active, uint32_t* free_slot
 
 smcx_status smcx_batch_destroy(smcx_batch* b) {
   if (!b) return batch_fail(SMCX_EINVAL, "null batch");
+  if (b->in_flight) cudaEventSynchronize(b->ev_chunk);
+  if (b->side) cudaStreamSynchronize(b->side);
   drop_graph(b);
   for (cudaEvent_t ev : b->ev)
     if (ev) cudaEventDestroy(ev);
+  if (b->ev_chunk) cudaEventDestroy(b->ev_chunk);
+  if (b->side) cudaStreamDestroy(b->side);
+  if (b->h_status) cudaFreeHost(b->h_status);
   delete b;
   return SMCX_OK;
 }

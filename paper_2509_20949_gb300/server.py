@@ -5,9 +5,13 @@ waiting jobs whenever a job slot and room in the device arena (the HBM
 budget) are free, keeps every admitted lattice resident on the device
 between chunks, runs one graph-captured chunk of sweeps for all resident
 jobs at a time (new arrivals join at the next chunk boundary), returns each
-finished job's result to the host and frees its space.  Each job's result is
-bit-identical to the same lattice run alone (the batch runtime guarantees
-it).  Latency = time from arrival to the result on the host.
+finished job's result to the host and frees its space.  Host work overlaps
+the device: while a chunk runs, arrivals are admitted (their uploads and
+initial energies on the batch's side stream) and the jobs finished by the
+previous chunk are read back, so the next chunk starts as soon as this one
+ends.  Each job's result is bit-identical to the same lattice run alone (the
+batch runtime guarantees it).  Latency = time from arrival to the result on
+the host.
 """
 from __future__ import annotations
 
@@ -71,23 +75,23 @@ class Server:
             remaining = collections.deque((t, j, a, b + 1) for (t, j, a, b) in remaining)
         self.queue = remaining
 
-    def step(self) -> int:
-        """Admit, run one chunk, collect finished jobs.  Returns jobs finished."""
-        self._admit()
-        if not self.running:
-            return 0
-        self.batch.run(self.chunk)
-        self.chunks += 1
-        for jid, (_, job, _) in self.running.items():  # every running job advanced
+    def _account(self, jids):
+        """Advances the progress (sweeps launched) of the jobs of a chunk as it
+        is launched: a job whose last chunk is on the device is not active."""
+        for jid in jids:
+            _, job, _ = self.running[jid]
             ran = min(self.chunk, job["sweeps"] - self.progress[jid])
             self.progress[jid] += ran
             self.swaps += _sites(job) * ran
-        finished = self.batch.poll()
-        now = self.clock()
-        for jid in finished:
+
+    def _collect(self):
+        """Reads back, frees and records every job finished by a completed
+        chunk (through the side stream while a chunk runs)."""
+        for jid in self.batch.poll():
             ticket, job, arr = self.running.pop(jid)
             r = self.batch.result(jid)
             self.batch.remove(jid)
+            now = self.clock()
             r["job"] = job.get("job", ticket)
             r["latency_s"] = now - arr
             r["arrival_s"] = arr
@@ -95,30 +99,70 @@ class Server:
             self.done[ticket] = r
             self.progress.pop(jid, None)
             self.swaps_finished += _sites(job) * job["sweeps"]
-        return len(finished)
+
+    def _active(self):
+        return [jid for jid, (_, job, _) in self.running.items()
+                if self.progress[jid] < job["sweeps"]]
+
+    def step(self) -> int:
+        """Admit, run one chunk to completion, collect finished jobs.
+        Returns the jobs finished."""
+        self._admit()
+        jids = self._active()
+        if not jids:
+            return 0
+        self.batch.run(self.chunk)
+        self.chunks += 1
+        self._account(jids)
+        before = len(self.done)
+        self._collect()
+        return len(self.done) - before
 
     def idle(self) -> bool:
         return not self.queue and not self.running
 
     def run_trace(self, jobs: list, window_s: float | None = None, drain: bool = True,
                   deadline_s: float | None = None):
-        """Replays an arrival trace (each job has arrival_s) in real time.
+        """Replays an arrival trace (each job has arrival_s) in real time,
+        overlapping each chunk with the admissions and read-backs around it.
         Returns the metrics of the completed jobs."""
         t0 = self.clock()
         pending = sorted(jobs, key=lambda j: j["arrival_s"])
         k = 0
-        while True:
+        flight = None  # job ids of the chunk on the device
+
+        def arrive():
+            nonlocal k
             now = self.clock() - t0
             while k < len(pending) and pending[k]["arrival_s"] <= now:
                 self.submit(pending[k], arrival=t0 + pending[k]["arrival_s"])
                 k += 1
-            if self.running or self.queue:
-                self.step()
-            elif k < len(pending):
-                time.sleep(max(0.0, min(0.01, pending[k]["arrival_s"] - now)))
-            if k >= len(pending) and (not drain or self.idle()):
+
+        while True:
+            arrive()
+            if flight is not None:
+                # while the chunk runs: admit arrivals for the next chunk and
+                # read back the jobs finished by the previous one
+                self._admit()
+                self._collect()
+                self.batch.wait()
+                flight = None
+            self._admit()
+            jids = self._active()
+            if jids:
+                self.batch.launch(self.chunk)
+                self._account(jids)
+                self.chunks += 1
+                flight = jids
+            else:
+                self._collect()
+                if k < len(pending) and not self.running:
+                    time.sleep(max(0.0, min(0.01, pending[k]["arrival_s"] - (self.clock() - t0))))
+            if flight is None and k >= len(pending) and (not drain or self.idle()):
                 break
             if deadline_s is not None and self.clock() - t0 > deadline_s:
+                if flight is not None:
+                    self.batch.wait()
                 break
         elapsed = self.clock() - t0
         return self.metrics(elapsed, submitted=k)

@@ -11,7 +11,13 @@ one, bit for bit:
 * after each half sweep the two ranks at an ownership boundary trade the
   2 x halo planes around it and merge them as mine ^ theirs ^ before;
 * when the grid moves for the next sweep, each rank fetches the planes of its
-  new window from their previous owners.
+  new window from their previous owners;
+* computation-communication overlap (Sec. 3.1): link-cell planes of one z
+  parity never interact either, so a half sweep may run plane by plane.  A
+  rank sweeps (all four colours of the half) its first and last plane of
+  that parity -- the only ones that write or read the boundary regions --
+  sends those regions, and sweeps its interior planes while they travel;
+  the merge waits for them.  The trajectory is the same.
 
 Every rank keeps a whole-lattice buffer (one byte per site: a 1e10-site
 lattice is 10 GB of a GPU's HBM) that is current on its window only.
@@ -60,7 +66,7 @@ class SlabSweep:
     a torch.distributed process group (default: the world, or one rank when
     torch.distributed is not initialised)."""
 
-    def __init__(self, lattice, group=None):
+    def __init__(self, lattice, group=None, overlap=True):
         import torch
         import torch.distributed as dist
 
@@ -80,6 +86,7 @@ class SlabSweep:
             raise ValueError("the z decomposition plans EPI link cells; the local-energy "
                              "model's cells are larger")
         self.n_z = int(lattice.desc.n[2])
+        self.overlap = bool(overlap)
         plan(lattice.desc, lattice.M, self.world, self.rank, 0)  # raises if the split is invalid
 
     # ------------------------------------------------------------------
@@ -116,11 +123,17 @@ class SlabSweep:
     def _p2p(self, sends, recvs):
         """sends: [(peer, tensor, tag)], recvs: [(peer, tensor, tag)], posted
         as one batch (NCCL groups them, so no pair waits on the other's order)."""
+        self._p2p_wait(self._p2p_post(sends, recvs))
+
+    def _p2p_post(self, sends, recvs):
         dist = self._dist
         ops = [dist.P2POp(dist.isend, t, self._global(p), self.group, tag) for p, t, tag in sends]
         ops += [dist.P2POp(dist.irecv, t, self._global(p), self.group, tag) for p, t, tag in recvs]
-        if ops:
-            for w in dist.batch_isend_irecv(ops):
+        return dist.batch_isend_irecv(ops) if ops else []
+
+    def _p2p_wait(self, works):
+        if works:
+            for w in works:
                 w.wait()
             self._after_comm()
 
@@ -137,9 +150,11 @@ class SlabSweep:
         hi = (p["z_lo"] + p["n_own"] - h) % self.n_z
         return lo, hi, 2 * h
 
-    def _merge_boundaries(self, p, before):
+    def _merge_boundaries(self, p, before, overlapped=None):
         """Trades the planes around both ownership boundaries with the two
-        neighbours and merges them (each site changed on one side at most)."""
+        neighbours and merges them (each site changed on one side at most).
+        overlapped(): work to run while the planes travel (no part of it may
+        read or write them)."""
         lo, hi, nb = self._regions(p)
         lat = self.lat
         mine_lo = lat.get_planes(lo, nb, lat.planes_buffer(nb))
@@ -148,13 +163,29 @@ class SlabSweep:
         up, down = (self.rank + 1) % self.world, (self.rank - 1) % self.world
         theirs_lo, theirs_hi = self._wire_empty(nb), self._wire_empty(nb)
         # my upper region goes up (the upper rank's lower one), my lower one down
-        self._p2p([(up, self._wire(mine_hi), _TAG_UP), (down, self._wire(mine_lo), _TAG_DOWN)],
-                  [(down, theirs_lo, _TAG_UP), (up, theirs_hi, _TAG_DOWN)])
+        works = self._p2p_post(
+            [(up, self._wire(mine_hi), _TAG_UP), (down, self._wire(mine_lo), _TAG_DOWN)],
+            [(down, theirs_lo, _TAG_UP), (up, theirs_hi, _TAG_DOWN)])
+        if overlapped is not None:
+            overlapped()
+        self._p2p_wait(works)
         if not self.device_comm:
             theirs_lo = self._to_lattice(theirs_lo, nb)
             theirs_hi = self._to_lattice(theirs_hi, nb)
         lat.merge_planes(lo, nb, theirs_lo, before[0])
         lat.merge_planes(hi, nb, theirs_hi, before[1])
+
+    @staticmethod
+    def _half_planes(c_lo, c_hi, half):
+        """This rank's link-cell planes of z parity `half` in [c_lo, c_hi) as
+        (boundary runs, interior run or None): the first and the last plane
+        are the boundary ones, the planes between them the interior."""
+        first = c_lo if c_lo % 2 == half else c_lo + 1
+        last = c_hi - 1 if (c_hi - 1) % 2 == half else c_hi - 2
+        if last < first:
+            return [], None
+        runs = [(first, first + 1)] + ([(last, last + 1)] if last > first else [])
+        return runs, ((first + 1, last) if last - first >= 4 else None)
 
     def _move(self, t):
         """After sweep t: every rank fetches the planes of its sweep-(t+1)
@@ -205,18 +236,30 @@ class SlabSweep:
                 T = T_first + (T_last - T_first) * i / (n_sweeps - 1)
             t = lat.sweep_counter
             p = self.plan(t)
-            for half in (0, 1):
-                before = None
-                if self.world > 1:
-                    lo, hi, nb = self._regions(p)
-                    before = (lat.get_planes(lo, nb, lat.planes_buffer(nb)),
-                              lat.get_planes(hi, nb, lat.planes_buffer(nb)))
-                for colour in range(4 * half, 4 * half + 4):
-                    st = lat.run_colour_planes(colour, T, p["c_lo"], p["c_hi"])
+            def run(c0, c1, colours):
+                nonlocal tot
+                for colour in colours:
+                    st = lat.run_colour_planes(colour, T, c0, c1)
                     tot += np.array([st["attempts"], st["unlike"], st["accepted"], st["sum_dE"]],
                                     dtype=np.int64)
-                if self.world > 1:
+
+            for half in (0, 1):
+                colours = range(4 * half, 4 * half + 4)
+                if self.world == 1:
+                    run(p["c_lo"], p["c_hi"], colours)
+                    continue
+                lo, hi, nb = self._regions(p)
+                before = (lat.get_planes(lo, nb, lat.planes_buffer(nb)),
+                          lat.get_planes(hi, nb, lat.planes_buffer(nb)))
+                if not self.overlap:
+                    run(p["c_lo"], p["c_hi"], colours)
                     self._merge_boundaries(p, before)
+                    continue
+                bounds, inner = self._half_planes(p["c_lo"], p["c_hi"], half)
+                for c0, c1 in bounds:
+                    run(c0, c1, colours)
+                self._merge_boundaries(p, before,
+                                       (lambda: run(inner[0], inner[1], colours)) if inner else None)
             lat.sweep_counter = t + 1
             if self.world > 1:
                 self._move(t)

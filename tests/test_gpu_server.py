@@ -52,3 +52,46 @@ def test_served_results_equal_alone_runs():
         occ, st, E = _alone(job)
         assert np.array_equal(r["occ"], occ), ticket
         assert r["stats"] == st and r["energy"] == E and r["sweeps"] == job["sweeps"]
+
+
+def test_launch_wait_overlap_admission_and_readback():
+    """Chunks launched without waiting (smcx_batch_launch / smcx_batch_wait):
+    while one runs, a new job is admitted through the side stream and a job
+    finished by an earlier chunk is read back; every job still ends in the
+    bits of its run alone."""
+    require_cuda()
+    from paper_2509_20949_gb300.batch import Batch
+    jobs = _trace(6, 9)
+    jobs[0]["sweeps"] = 8                       # finishes in the first chunks
+    for j in jobs[1:]:
+        j["sweeps"] = max(j["sweeps"], 40)
+    transfer = max(inputs.n_sites(j["kind"], j["n"]) for j in jobs)
+    heap = sum(Batch.job_bytes(j["kind"], j["n"], j["K"]) for j in jobs)
+    b = Batch(8, Batch.control_bytes(8, transfer) + heap + (1 << 20), transfer)
+    # slot ids are reused after remove: keep the slot -> job map current
+    slot_job = {b.add(j["kind"], j["n"], j["K"], j["occ"], j["V"], j["T"], j["sweeps"],
+                      seed=j["seed"]): k for k, j in enumerate(jobs[:4])}
+    results, launched_while_busy = {}, 0
+    late = {k: j for k, j in enumerate(jobs) if k >= 4}
+    for _ in range(400):
+        b.launch(4)
+        if late and b.tuning()["tuned"]:
+            k, j = late.popitem()               # admitted while the chunk runs
+            slot_job[b.add(j["kind"], j["n"], j["K"], j["occ"], j["V"], j["T"], j["sweeps"],
+                           seed=j["seed"])] = k
+            launched_while_busy += 1
+        for jid in b.poll():                    # finished by an earlier chunk
+            results[slot_job.pop(jid)] = b.result(jid)
+            b.remove(jid)
+        b.wait()
+        if len(results) == len(jobs):
+            break
+    for jid in b.poll():
+        results[slot_job.pop(jid)] = b.result(jid)
+    assert launched_while_busy == 2 and len(results) == len(jobs)
+    for k, job in enumerate(jobs):
+        occ, st, E = _alone(job)
+        r = results[k]
+        assert np.array_equal(r["occ"], occ), k
+        assert r["stats"] == st and r["energy"] == E and r["sweeps"] == job["sweeps"], k
+    b.close()
