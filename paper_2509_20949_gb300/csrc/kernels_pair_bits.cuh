@@ -2,9 +2,11 @@
 // (Warren-Cowley SRO, Sec. 3.2, Eq. 9, and the EPI energy, Sec. 3) for
 // 8-bit storage.
 //
-// Output as the tiled pair-count kernel: H_m[p'][p] = #{(i, d): d in S_m+,
-// sigma_i = p', sigma_{i+d} = p} over the lexicographically positive half
-// S_m+ of each shell (the host forms N_m = H_m + H_m^T), rows of KMAX species.
+// Output: rows of KMAX species per shell holding an upper-triangular U_m
+// with U_m + U_m^T = N_m, the full-shell directed counts N_m[p'][p] = #{(i,
+// d): d in S_m, sigma_i = p', sigma_{i+d} = p}, which is all the callers use
+// (they form H + H^T of the tiled kernel's half-shell counts H, and N of a
+// symmetric count is U + U^T as well).
 //
 // Counting by bit masks.  A warp turns 128 consecutive sites of a lattice
 // row (a span) into one 32-bit mask per species and byte lane: lane i loads
@@ -12,15 +14,16 @@
 // j of the span, bit i <-> site 128 s + 4 i + j.  The site one further in x
 // is then plane j + 1 of the same bit, or, from plane 3, plane 0 of the next
 // bit (a one-bit funnel shift across spans), so a half-shell neighbour's
-// masks are plane re-indexing plus at most one shift.  H_m[p'][p] for p', p
-// < KMAX - 1 is the sum of popc(centre mask p' & neighbour mask p) over
-// planes, spans and vectors.  The row and column of the last species follow
-// from the species counts c: every site is the neighbour of exactly one
-// centre per vector (periodic translation is a bijection), so
-// sum_p' H_m[p'][p] = c_p z_m/2 and sum_p H_m[p'][p] = c_p' z_m/2 -- a
-// one-thread kernel fills them in.  A block owns boxes of whole x rows by
-// BY x BZ rows (persistent grid); the masks of the box plus a halo of H rows
-// in y and z (periodic) sit in shared memory.
+// masks are plane re-indexing plus at most one shift.  Over the half shell
+// S_m+ (the other half is the same bonds seen from the far end), for p < q
+// < KMAX - 1, N_m[p][q] = N_m[q][p] = sum of popc((c_p & n_q) | (c_q & n_p))
+// (centre masks c, neighbour masks n; c_p and c_q are disjoint) over
+// planes, spans and vectors, stored as U[p][q]; U[p][p] = N_m[p][p] / 2 =
+// sum of popc(c_p & n_p).  The last species' entries follow from the
+// species counts: every site has z_m shell-m neighbours, so row p of N_m
+// sums to c_p z_m -- a one-thread kernel fills them in.  A block owns boxes
+// of whole x rows by BY x BZ rows (persistent grid); the masks of the box
+// plus a halo of H rows in y and z (periodic) sit in shared memory.
 #pragma once
 
 #include <utility>
@@ -115,10 +118,15 @@ __device__ __forceinline__ void count_vec(const uint32_t (&cm)[4][C::NQ], const 
 #pragma unroll
       for (int q = 0; q < C::NQ; ++q) nm[q] = __funnelshift_r(lo[q], hi[q], 1);
     }
+    // a site has one species, so the centre masks of p and q are disjoint
+    // and one popc of the union counts both orientations of the pair
 #pragma unroll
-    for (int p = 0; p < C::NQ; ++p)
+    for (int p = 0; p < C::NQ; ++p) {
+      acc[p][p] += __popc(cm[j][p] & nm[p]);
 #pragma unroll
-      for (int q = 0; q < C::NQ; ++q) acc[p][q] += __popc(cm[j][p] & nm[q]);
+      for (int q = p + 1; q < C::NQ; ++q)
+        acc[p][q] += __popc((cm[j][p] & nm[q]) | (cm[j][q] & nm[p]));
+    }
   }
 }
 
@@ -224,7 +232,7 @@ __global__ void __launch_bounds__(C::NT) k_pair_count_bits(const __grid_constant
 #pragma unroll
       for (int p = 0; p < C::NQ; ++p)
 #pragma unroll
-        for (int q = 0; q < C::NQ; ++q) acc[p][q] = 0;
+        for (int q = p; q < C::NQ; ++q) acc[p][q] = 0;
       auto basis = [&](auto bconst) {
         constexpr int B = decltype(bconst)::value;
         for (int it = tid; it < n_items; it += C::NT) {
@@ -262,7 +270,7 @@ __global__ void __launch_bounds__(C::NT) k_pair_count_bits(const __grid_constant
 #pragma unroll
       for (int p = 0; p < C::NQ; ++p)
 #pragma unroll
-        for (int q = 0; q < C::NQ; ++q) {
+        for (int q = p; q < C::NQ; ++q) {
           const uint32_t v = __reduce_add_sync(0xffffffffu, acc[p][q]);
           if (lane == 0 && v) atomicAdd(&s_cnt[(Mm * C::NQ + p) * C::NQ + q], v);
         }
@@ -289,8 +297,10 @@ __global__ void __launch_bounds__(C::NT) k_pair_count_bits(const __grid_constant
       atomicAdd(&hcnt[p * C::KMAX + KM], static_cast<unsigned long long>(s_cnt[C::NCNT + p]));
 }
 
-// The last species' row and column of every H_m from the species counts
-// (one thread; see the header comment).
+// The last species' row and column of every U_m from the species counts
+// (one thread; see the header comment).  With N = U + U^T, row p of N sums
+// to c_p z_m (z_m = the full shell): N_m[p][KMAX-1] = c_p z_m - sum_{q <
+// KMAX-1} N_m[p][q], and N_m[KMAX-1][KMAX-1] (even) from the last row.
 template <class C>
 __global__ void k_pair_bits_finish(unsigned long long* __restrict__ h, unsigned long long n_sites) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
@@ -303,21 +313,17 @@ __global__ void k_pair_bits_finish(unsigned long long* __restrict__ h, unsigned 
   }
   c[KM] = rest;
   for (int m = 0; m < C::M; ++m) {
-    const unsigned long long z = static_cast<unsigned long long>(shell_z(C::KIND, m) / 2);
-    unsigned long long* hm = h + m * C::KMAX * C::KMAX;
-    for (int p = 0; p < KM; ++p) {
-      unsigned long long row = 0;
-      for (int q = 0; q < KM; ++q) row += hm[p * C::KMAX + q];
-      hm[p * C::KMAX + KM] = c[p] * z - row;
-    }
+    const unsigned long long z = static_cast<unsigned long long>(shell_z(C::KIND, m));
+    unsigned long long* um = h + m * C::KMAX * C::KMAX;
     unsigned long long last = 0;
-    for (int q = 0; q < KM; ++q) {
-      unsigned long long col = 0;
-      for (int p = 0; p < KM; ++p) col += hm[p * C::KMAX + q];
-      hm[KM * C::KMAX + q] = c[q] * z - col;
-      last += hm[KM * C::KMAX + q];
+    for (int p = 0; p < KM; ++p) {
+      unsigned long long row = 0;  // sum over q < KM of N[p][q]
+      for (int q = 0; q < KM; ++q)
+        row += q == p ? 2 * um[p * C::KMAX + p] : um[min(p, q) * C::KMAX + max(p, q)];
+      um[p * C::KMAX + KM] = c[p] * z - row;
+      last += um[p * C::KMAX + KM];
     }
-    hm[KM * C::KMAX + KM] = c[KM] * z - last;
+    um[KM * C::KMAX + KM] = (c[KM] * z - last) / 2;
   }
 }
 
