@@ -368,11 +368,13 @@ const char* smcx_last_error(void);
    simulations at different temperatures or compositions share nothing) run
    together.  Work items are 32 active link cells of one job and colour
    phase, one per lane of a warp.  Two schedules: a chunk of sweeps of all
-   active jobs as one launch of a persistent kernel whose warps take items
-   from a queue in phase order, a per-job counter of finished items keeping
-   each job's colour phases in sequence (bounded waits: a wait that gives up
-   fails the run with ETIMEOUT); or one launch per colour phase covering all
-   jobs.  The schedule, item shape and register budget are tuned online.
+   active jobs as one cooperative launch of a persistent kernel following a
+   plan built on the host -- every warp owns fixed ranges of items of some
+   jobs, the same in every colour phase, the jobs with the longest chains of
+   dependent trials spread first -- with a per-job counter of finished items
+   keeping each job's colour phases in sequence (bounded waits: a wait that
+   gives up fails the run with ETIMEOUT); or one launch per colour phase
+   covering all jobs.  The schedule, item shape and register budget are tuned online.
    With a stream the chunk is captured into a CUDA graph.  Each job's trajectory is
    bit-identical to the same lattice run alone through smcx_sweep (same
    seed, temperature and sweep counter), whatever the tuning.  Jobs use 8-bit
@@ -438,9 +440,9 @@ smcx_status smcx_batch_wait(smcx_batch* b, uint32_t* n_finished);
 
 /* Tuning of the batched sweep (never changes results):
      SMCX_BATCH_OPT_TILE       work-item shape index (see smcx_batch_tile_shape)
-     SMCX_BATCH_OPT_SCHEDULE   0 = persistent work queue (one launch per
-                               chunk, per-job phase counters), 1 = one launch
-                               per colour phase for all jobs
+     SMCX_BATCH_OPT_SCHEDULE   0 = persistent plan (one cooperative launch
+                               per chunk, per-job phase counters), 1 = one
+                               launch per colour phase for all jobs
      SMCX_BATCH_OPT_OCCUPANCY  register budget index: 0, 1 = 3, 4 resident
                                blocks of 128 threads per SM
    Value -1 (the default) = chosen online.  Setting any restarts the online
@@ -449,7 +451,7 @@ smcx_status smcx_batch_wait(smcx_batch* b, uint32_t* n_finished);
 #define SMCX_BATCH_OPT_OCCUPANCY 2u
 #define SMCX_BATCH_OPT_SCHEDULE 3u
 /* Testing aid for failure detection (value 1 arms it): the next run with the
-   persistent-queue schedule tells the kernel that the first active job has
+   persistent schedule tells the kernel that the first active job has
    one work item per phase more than it has, so the waits for that job's
    earlier phases give up after their limit (about 2 s); the run returns
    ETIMEOUT and the batch stays in an error state.  Nothing faults or hangs. */
@@ -482,10 +484,10 @@ smcx_status smcx_batch_exchange(smcx_batch* b, uint32_t* ladder, uint32_t n, uin
 /* Current temperature of a job (changes through smcx_batch_exchange). */
 smcx_status smcx_batch_temperature(smcx_batch* b, uint32_t job_id, double* T);
 
-/* Work-queue statistics since the batch was created: out[0] = work items
-   that had to wait for the previous colour phase of their job, out[1] =
-   polls of those waits, out[2] = nanoseconds they waited (summed over
-   warps).  Synchronises. */
+/* Persistent-schedule statistics since the batch was created: out[0] =
+   item ranges that had to wait for the previous colour phase of their job,
+   out[1] = polls of those waits, out[2] = nanoseconds they waited (summed
+   over warps).  Synchronises. */
 smcx_status smcx_batch_queue_stats(smcx_batch* b, uint64_t* out);
 
 /* Active link cells (x, y, z) of work-item shape i (product 32): shape 0

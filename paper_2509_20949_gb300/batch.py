@@ -131,7 +131,7 @@ class Batch:
 
     def set_option(self, key: int, value: int):
         """key OPT_TILE (work-item shape index), OPT_SCHEDULE (0 persistent
-        queue, 1 one launch per colour phase) or OPT_OCCUPANCY (register
+        plan, 1 one launch per colour phase) or OPT_OCCUPANCY (register
         budget index); value -1 = tuned online."""
         check(self.L.smcx_batch_set_option(self.h, int(key), int(value)))
 
@@ -149,8 +149,9 @@ class Batch:
         return tuple(int(v) for v in c)
 
     def queue_stats(self):
-        """Items that waited for their job's previous phase, their polls and
-        the nanoseconds waited (summed over warps), since creation."""
+        """Item ranges of the persistent schedule that waited for their job's
+        previous phase, their polls and the nanoseconds waited (summed over
+        warps), since creation."""
         out = (ctypes.c_uint64 * 3)()
         check(self.L.smcx_batch_queue_stats(self.h, out))
         return dict(waited_items=int(out[0]), polls=int(out[1]), wait_ns=int(out[2]))

@@ -6,7 +6,7 @@
 // shared-memory tiles: they stay in L2) and for batches of many jobs, whose
 // work items (32 cells of one job and colour phase, one per lane) are run
 // either by one launch per colour phase or by one persistent launch per
-// chunk of sweeps (k_sweep_cells_phase / k_sweep_cells_queue).  Works on any
+// chunk of sweeps following a plan (k_sweep_cells_phase / k_sweep_cells_queue).  Works on any
 // lattice with at least 4 conventional cells per dimension (then no two
 // shell vectors reach the same site, so the swapped pair's mutual bond is
 // the only term to remove from the raw neighbour counts).
@@ -375,20 +375,27 @@ struct JobDev {
   uint32_t A[3];                // active cells of a colour along each axis
 };
 
-// The chunk's work queue.  Item i is item k = i mod n_items of colour phase
-// ph = i / n_items (sweep ph / 8, colour ph mod 8); within a phase the items
-// of the active jobs follow one another in `order`.  An item is 32 active
-// cells of one job, one per lane of a warp: with tx < 0 the next 32 cells of
-// the colour in x-fastest order, else a box of 2^tx x 2^ty x 2^(5-tx-ty)
-// cells of the colour's active-cell grid.
+// The chunk's work.  Within a colour phase the items of the active jobs
+// follow one another in `order` (the phase-synchronous schedule runs item k
+// of every phase on warp k).  An item is 32 active cells of one job, one per
+// lane of a warp: with tx < 0 the next 32 cells of the colour in x-fastest
+// order, else a box of 2^tx x 2^ty x 2^(5-tx-ty) cells of the colour's
+// active-cell grid.  The persistent schedule follows a plan: warp w of the
+// grid owns segments seg[wfirst[w] .. wfirst[w+1]) -- a segment is a range
+// of consecutive items (x = job slot, y = first item, z = items) -- and runs
+// them for every colour phase of the chunk in turn, the same items in every
+// phase.
 struct QueueArgs {
   const JobDev* jobs;
   const uint32_t* order;        // slots of the active jobs
   const uint32_t* first;        // first item of order[a] within a phase; first[n_active] = n_items
   uint32_t n_active;
   uint32_t n_items;
-  unsigned long long n_total;   // n_items * 8 * (sweeps of the chunk)
-  unsigned long long* ctr;      // [0] queue head, [1] status, [2 + slot] items finished per job
+  const uint4* seg;             // persistent plan: segments
+  const uint32_t* wfirst;       // first segment of each warp; wfirst[n_warps] = segments
+  uint32_t n_warps;             // warps of the plan (the persistent grid's)
+  uint32_t n_ph;                // colour phases of the chunk (8 x its sweeps)
+  unsigned long long* ctr;      // [1] status, [2 + slot] items finished per job
   unsigned long long* qstats;   // [0] items that waited, [1] polls, [2] ns waited
   int tx, ty;
 };
@@ -396,12 +403,7 @@ struct QueueArgs {
 constexpr unsigned long long kQueueTimeout = 1;        // status: a wait gave up
 constexpr unsigned long long kWaitLimitNs = 2000000000ull;  // 2 s per wait
 constexpr uint32_t kWaitMaxPolls = 1u << 24;                // and at most this many polls
-// per-warp shared tables of the batched kernel: thresholds, then the largest
-// difference table (K = 6, M = 4)
-constexpr int kQueueDBytes = 6 * 6 * 160;
-constexpr int kQueueWarpBytes = 4 * kTabWords + kQueueDBytes;
-constexpr int kQueueWarps = 4;
-constexpr int kQueueSmem = kQueueWarps * kQueueWarpBytes;  // dynamic shared memory per block
+constexpr int kQueueWarps = 4;  // warps per block of either batched schedule
 
 __device__ __forceinline__ unsigned long long globaltimer_ns() {
   unsigned long long t;
@@ -487,22 +489,17 @@ __device__ __forceinline__ uint32_t queue_job(const QueueArgs& q, uint32_t k, ui
   return __ldg(q.order + lo);
 }
 
-// the job's geometry and tables into the warp's shared slot, unless the
-// warp's previous item was of the same job (warp-uniform)
+// the job's geometry into the warp's shared slot, unless the warp's previous
+// item was of the same job (warp-uniform).  The job's threshold and
+// difference tables are read where they are, in global memory, through L1:
+// a per-warp shared copy (12 KB) would leave the SM's L1 too small for the
+// lattices of the jobs it runs.
 __device__ __forceinline__ void queue_load_job(const JobDev* J, uint32_t slot, uint32_t* cur,
-                                               Geom* g, uint8_t* w_smem, int lane) {
+                                               Geom* g, int lane) {
   if (slot == *cur) return;
   const uint32_t* gsrc = reinterpret_cast<const uint32_t*>(&J->g);
   uint32_t* gdst = reinterpret_cast<uint32_t*>(g);
   for (int w = lane; w < static_cast<int>(sizeof(Geom) / 4); w += 32) gdst[w] = __ldg(gsrc + w);
-  const uint4* tsrc = reinterpret_cast<const uint4*>(
-      __ldg(reinterpret_cast<const unsigned long long*>(&J->tab)));
-  const uint4* dsrc = reinterpret_cast<const uint4*>(
-      __ldg(reinterpret_cast<const unsigned long long*>(&J->dtab)));
-  uint4* tdst = reinterpret_cast<uint4*>(w_smem);
-  for (int w = lane; w < kTabWords / 4; w += 32) tdst[w] = __ldg(tsrc + w);
-  uint4* ddst = reinterpret_cast<uint4*>(w_smem + 4 * kTabWords);
-  for (int w = lane; w < kQueueDBytes / 16; w += 32) ddst[w] = __ldg(dsrc + w);
   *cur = slot;
   __syncwarp();
 }
@@ -511,9 +508,11 @@ __device__ __forceinline__ void queue_load_job(const JobDev* J, uint32_t slot, u
 // job J, one per lane, then the warp's statistics into the job's counters.
 __device__ __forceinline__ void queue_run_item(const QueueArgs& q, const JobDev* J, uint32_t ph,
                                                uint32_t li, int lane, const Geom& g,
-                                               const uint8_t* w_smem, const int* s_pt) {
-  const uint32_t* const s_tab = reinterpret_cast<const uint32_t*>(w_smem);
-  const uint8_t* const s_d = w_smem + 4 * kTabWords;
+                                               const int* s_pt) {
+  const uint32_t* const s_tab =
+      reinterpret_cast<const uint32_t*>(__ldg(reinterpret_cast<const unsigned long long*>(&J->tab)));
+  const uint8_t* const s_d =
+      reinterpret_cast<const uint8_t*>(__ldg(reinterpret_cast<const unsigned long long*>(&J->dtab)));
   const int colour = static_cast<int>(ph & 7u);
   const uint32_t A0 = __ldg(&J->A[0]), A1 = __ldg(&J->A[1]);
   uint32_t a[3];
@@ -573,59 +572,59 @@ __device__ __forceinline__ void queue_run_item(const QueueArgs& q, const JobDev*
 }
 
 // Persistent schedule: every colour phase of a chunk of sweeps of every job
-// of a batch in one launch.  Warps take items from the queue in order;
-// before it starts an item of phase ph of a job, a warp waits (bounded)
-// until all items of the job's phases before ph have finished.  Items are
-// handed out in increasing order and a warp only waits for items handed out
-// before its own, all of them held by running warps, so the waits always
-// end.  A finished item is released (warp barrier, fence, counter
-// increment); the waiting lane polls the count with relaxed loads and fences
-// once it has seen it (acquire), then the warp barrier passes that on to the
-// other lanes.
+// of a batch in one launch.  Each warp runs its segments of the plan phase
+// by phase, in plan order (a segment's items are the same in every phase,
+// so a warp keeps coming back to the same part of the same lattice and
+// finds it in its SM's L1).  Before a segment of phase ph, the warp waits
+// (bounded) until all items of the job's phase ph - 1 have finished,
+// wherever they run.  The launch is cooperative, so every warp of the plan
+// is resident; a warp waits only for items of an earlier phase, which every
+// other warp reaches before any item of a later one, so by induction over
+// the phases every wait ends.  A finished segment is released (warp
+// barrier, fence, counter increment); the waiting lane polls the count with
+// relaxed loads and fences once it has seen it (acquire), then the warp
+// barrier passes that on to the other lanes.
 template <int MINB>
 __global__ void __launch_bounds__(32 * kQueueWarps, MINB)
     k_sweep_cells_queue(const __grid_constant__ QueueArgs q) {
-  extern __shared__ __align__(16) uint8_t q_smem[];
   __shared__ QueueShared sh;
   queue_block_init(sh);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  uint8_t* const w_smem = q_smem + warp * kQueueWarpBytes;
-  unsigned long long* const head = q.ctr;
+  const uint32_t gw = blockIdx.x * kQueueWarps + warp;
+  if (gw >= q.n_warps) return;
   unsigned long long* const status = q.ctr + 1;
   unsigned long long* const done = q.ctr + 2;
+  const uint32_t s0 = __ldg(q.wfirst + gw), s1 = __ldg(q.wfirst + gw + 1);
   uint32_t cur = 0xFFFFFFFFu;
-  for (;;) {
-    unsigned long long i = 0;
-    int stop = 0;
-    if (lane == 0) {
-      stop = ld_relaxed(status) != 0;
-      if (!stop) i = atomicAdd(head, 1ull);
-    }
-    stop = __shfl_sync(0xffffffffu, stop, 0);
-    i = __shfl_sync(0xffffffffu, i, 0);
-    if (stop || i >= q.n_total) break;
-    const uint32_t ph = static_cast<uint32_t>(i / q.n_items);
-    const uint32_t k = static_cast<uint32_t>(i - static_cast<unsigned long long>(ph) * q.n_items);
-    uint32_t li;
-    const uint32_t slot = queue_job(q, k, &li);
-    const JobDev* J = q.jobs + slot;
-    if ((ph >> 3) >= __ldg(&J->sweeps)) continue;  // the job stops earlier; nobody waits for it
-    queue_load_job(J, slot, &cur, &sh.g[warp], w_smem, lane);
-    int ok = 1;
-    if (lane == 0 && ph != 0) {
-      ok = wait_at_least(done + slot, static_cast<unsigned long long>(ph) * __ldg(&J->items), status,
-                         q.qstats);
-      if (ok) __threadfence();
-      else atomicExch(status, kQueueTimeout);
-    }
-    ok = __shfl_sync(0xffffffffu, ok, 0);
-    if (!ok) break;
-    __syncwarp();
-    queue_run_item(q, J, ph, li, lane, sh.g[warp], w_smem, sh.pt);
-    __syncwarp();
-    if (lane == 0) {
-      __threadfence();
-      atomicAdd(done + slot, 1ull);
+  for (uint32_t ph = 0; ph < q.n_ph; ++ph) {
+    for (uint32_t s = s0; s < s1; ++s) {
+      const uint4 sg = __ldg(q.seg + s);
+      const JobDev* J = q.jobs + sg.x;
+      if ((ph >> 3) >= __ldg(&J->sweeps)) continue;  // the job stops earlier; nobody waits for it
+      int stop = 0;
+      if (lane == 0) {
+        stop = ld_relaxed(status) != 0;
+        if (!stop && ph != 0) {
+          if (wait_at_least(done + sg.x, static_cast<unsigned long long>(ph) * __ldg(&J->items),
+                            status, q.qstats))
+            __threadfence();
+          else {
+            atomicExch(status, kQueueTimeout);
+            stop = 1;
+          }
+        }
+      }
+      stop = __shfl_sync(0xffffffffu, stop, 0);
+      if (stop) return;
+      queue_load_job(J, sg.x, &cur, &sh.g[warp], lane);
+      __syncwarp();
+      for (uint32_t li = sg.y; li < sg.y + sg.z; ++li)
+        queue_run_item(q, J, ph, li, lane, sh.g[warp], sh.pt);
+      __syncwarp();
+      if (lane == 0) {
+        __threadfence();
+        atomicAdd(done + sg.x, static_cast<unsigned long long>(sg.z));
+      }
     }
   }
 }
@@ -636,20 +635,18 @@ __global__ void __launch_bounds__(32 * kQueueWarps, MINB)
 template <int MINB>
 __global__ void __launch_bounds__(32 * kQueueWarps, MINB)
     k_sweep_cells_phase(const __grid_constant__ QueueArgs q, uint32_t ph) {
-  extern __shared__ __align__(16) uint8_t q_smem[];
   __shared__ QueueShared sh;
   queue_block_init(sh);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const uint32_t k = blockIdx.x * kQueueWarps + warp;
   if (k >= q.n_items) return;
-  uint8_t* const w_smem = q_smem + warp * kQueueWarpBytes;
   uint32_t li;
   const uint32_t slot = queue_job(q, k, &li);
   const JobDev* J = q.jobs + slot;
   if ((ph >> 3) >= __ldg(&J->sweeps)) return;
   uint32_t cur = 0xFFFFFFFFu;
-  queue_load_job(J, slot, &cur, &sh.g[warp], w_smem, lane);
-  queue_run_item(q, J, ph, li, lane, sh.g[warp], w_smem, sh.pt);
+  queue_load_job(J, slot, &cur, &sh.g[warp], lane);
+  queue_run_item(q, J, ph, li, lane, sh.g[warp], sh.pt);
 }
 
 }  // namespace cell

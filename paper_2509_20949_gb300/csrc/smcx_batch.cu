@@ -10,10 +10,12 @@
 // link cells of one job and colour phase (kernels_cell.cuh), ordered within
 // a phase with the jobs whose largest cells have the most trials first.  Two
 // schedules run a chunk of S sweeps of every active job: the persistent
-// queue (one launch; warps take items in phase order, a per-job counter of
-// finished items keeps each job's phases in sequence), or one launch per
-// colour phase for all jobs.  With a stream the chunk is captured into a
-// CUDA graph, replayed until the job set or the tuning changes.
+// schedule (one cooperative launch following a plan that gives every warp
+// fixed ranges of items, the same in every phase; a per-job counter of
+// finished items keeps each job's phases in sequence, so a job runs ahead of
+// the others as far as its own items allow), or one launch per colour phase
+// for all jobs.  With a stream the chunk is captured into a CUDA graph,
+// replayed until the job set or the tuning changes.
 //
 // Tuning (results never depend on it): item shape, schedule and register
 // budget are picked online.  While untuned, a run spends its first sweeps on
@@ -58,8 +60,8 @@ constexpr int kTiles[][2] = {{-1, 0}, {3, 2}, {2, 2}, {1, 2}};
 constexpr int kTileCount = 4;
 // register budgets: 3 or 4 resident blocks of 128 threads per SM
 constexpr int kOccCount = 2;
-// schedules: 0 = persistent work queue (one launch per chunk), 1 = one
-// launch per colour phase
+// schedules: 0 = persistent plan (one launch per chunk), 1 = one launch per
+// colour phase
 constexpr int kSchedCount = 2;
 constexpr int kDefaultTile = 0, kDefaultSched = 1, kDefaultOcc = 1;
 constexpr uint32_t kTuneSweeps = 2;  // sweeps per timed candidate
@@ -70,6 +72,9 @@ using PhaseLauncher = cudaError_t (*)(const void*, uint32_t, cudaStream_t);
 constexpr PhaseLauncher kPhaseLaunchers[] = {launch_sweep_phase_3, launch_sweep_phase_4};
 using QueueBlocks = int (*)();
 constexpr QueueBlocks kBlocks[] = {sweep_queue_blocks_3, sweep_queue_blocks_4};
+// capacity of the persistent plan: warps of the grid (4 per block) and
+// segments (at most two per warp plus one per job, see build_plan)
+constexpr uint32_t kPlanWarps = 16384;
 
 size_t aup(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
@@ -142,7 +147,7 @@ struct Job {
 };
 
 struct ControlLayout {
-  size_t jobs, tabs, dtabs, stats, order, first, ctr, qstats, pairs, flag, scratch;
+  size_t jobs, tabs, dtabs, stats, order, first, seg, wfirst, ctr, qstats, pairs, flag, scratch;
   size_t pairs2, flag2, scratch2;  // the side stream's (admission and results during a chunk)
   size_t heap;
 };
@@ -162,6 +167,10 @@ ControlLayout control_layout(uint32_t max_jobs, size_t transfer_bytes) {
   o += aup(sizeof(uint32_t) * max_jobs, kAlign);
   c.first = o;
   o += aup(sizeof(uint32_t) * (max_jobs + 1), kAlign);
+  c.seg = o;
+  o += aup(sizeof(uint4) * (2 * static_cast<size_t>(kPlanWarps) + max_jobs), kAlign);
+  c.wfirst = o;
+  o += aup(sizeof(uint32_t) * (kPlanWarps + 1), kAlign);
   c.ctr = o;
   o += aup(sizeof(unsigned long long) * (2 + max_jobs), kAlign);
   c.qstats = o;
@@ -271,6 +280,8 @@ struct smcx_batch {
   smcx_status sticky = SMCX_OK;
   std::vector<uint32_t> order;  // active slots (queue order)
   int queue_tile = -1;          // tile the device order/first arrays were built for
+  int plan_tile = -1, plan_occ = -1;  // tile and register budget of the device plan
+  uint32_t plan_warps = 0;      // warps of the device plan
   uint32_t n_items = 0;         // items of one phase over all active jobs
   Tuner tuner;
   cudaEvent_t ev[2] = {nullptr, nullptr};
@@ -370,7 +381,77 @@ smcx_status build_queue(smcx_batch* b, int tile) {
                                   cudaMemcpyHostToDevice, b->stream));
   }
   b->queue_tile = tile;
+  b->plan_tile = -1;
   b->dirty = false;
+  drop_graph(b);
+  return SMCX_OK;
+}
+
+// The persistent schedule's plan for tile `tile` on the grid of register
+// budget `occ`: every active job's items of a phase cut into ranges and each
+// range given to the warp with the least work so far (jobs in queue order,
+// the longest chains first), work = items x the job's longest cell.  A range
+// holds r = max(1, tau / c) items of a job whose largest cell has c trials,
+// tau = max(largest c, total work / warps), so no warp's range outlasts the
+// longest chain and there are at most 2 x warps + jobs ranges.  The same
+// plan serves every phase, so a warp returns to the same cells.
+smcx_status build_plan(smcx_batch* b, int tile, int occ) {
+  const uint32_t W = std::min<uint32_t>(static_cast<uint32_t>(b->grid[occ]) * cell::kQueueWarps,
+                                        kPlanWarps);
+  uint64_t total = 0, tau = 1;
+  for (uint32_t slot : b->order) {
+    const Job& j = b->jobs[slot];
+    const uint64_t c = longest_cell(j);
+    total += c * job_items(j, tile, nullptr, nullptr);
+    tau = std::max(tau, c);
+  }
+  tau = std::max<uint64_t>(tau, (total + W - 1) / W);
+  std::vector<std::vector<uint4>> per(W);
+  // least-loaded warp first (ties: lower index)
+  std::vector<std::pair<uint64_t, uint32_t>> heap;
+  heap.reserve(W);
+  for (uint32_t w = 0; w < W; ++w) heap.emplace_back(0, w);
+  auto later = [](const std::pair<uint64_t, uint32_t>& x, const std::pair<uint64_t, uint32_t>& y) {
+    return x > y;
+  };
+  size_t n_seg = 0;
+  for (uint32_t slot : b->order) {
+    const Job& j = b->jobs[slot];
+    const uint64_t c = longest_cell(j);
+    const uint32_t items = job_items(j, tile, nullptr, nullptr);
+    const uint32_t r = static_cast<uint32_t>(std::max<uint64_t>(1, tau / c));
+    for (uint32_t i0 = 0; i0 < items; i0 += r) {
+      const uint32_t n = std::min(r, items - i0);
+      std::pop_heap(heap.begin(), heap.end(), later);
+      auto& h = heap.back();
+      per[h.second].push_back(make_uint4(slot, i0, n, 0));
+      h.first += c * n;
+      std::push_heap(heap.begin(), heap.end(), later);
+      ++n_seg;
+    }
+  }
+  if (n_seg > 2 * static_cast<size_t>(kPlanWarps) + b->max_jobs)
+    return batch_fail(SMCX_EBUDGET, "persistent plan larger than its capacity");
+  std::vector<uint4> seg;
+  std::vector<uint32_t> wfirst;
+  seg.reserve(n_seg);
+  wfirst.reserve(W + 1);
+  for (uint32_t w = 0; w < W; ++w) {
+    wfirst.push_back(static_cast<uint32_t>(seg.size()));
+    seg.insert(seg.end(), per[w].begin(), per[w].end());
+  }
+  wfirst.push_back(static_cast<uint32_t>(seg.size()));
+  if (!seg.empty())
+    BATCH_CUDA(b, cudaMemcpyAsync(b->at(b->cl.seg), seg.data(), sizeof(uint4) * seg.size(),
+                                  cudaMemcpyHostToDevice, b->stream));
+  BATCH_CUDA(b, cudaMemcpyAsync(b->at(b->cl.wfirst), wfirst.data(),
+                                sizeof(uint32_t) * wfirst.size(), cudaMemcpyHostToDevice,
+                                b->stream));
+  // the host vectors must outlive the copies
+  BATCH_CUDA(b, cudaStreamSynchronize(b->stream));
+  b->plan_tile = tile;
+  b->plan_occ = occ;
+  b->plan_warps = W;
   drop_graph(b);
   return SMCX_OK;
 }
@@ -384,7 +465,10 @@ smcx_status enqueue_chunk(smcx_batch* b, uint32_t sweeps, int tile, int sched, i
   q.first = reinterpret_cast<const uint32_t*>(b->at(b->cl.first));
   q.n_active = static_cast<uint32_t>(b->order.size());
   q.n_items = b->n_items;
-  q.n_total = static_cast<unsigned long long>(b->n_items) * 8ull * sweeps;
+  q.seg = reinterpret_cast<const uint4*>(b->at(b->cl.seg));
+  q.wfirst = reinterpret_cast<const uint32_t*>(b->at(b->cl.wfirst));
+  q.n_warps = b->plan_warps;
+  q.n_ph = 8 * sweeps;
   q.ctr = b->ctr();
   q.qstats = b->qstats();
   q.tx = kTiles[tile][0];
@@ -392,7 +476,8 @@ smcx_status enqueue_chunk(smcx_batch* b, uint32_t sweeps, int tile, int sched, i
   if (sched == 0) {
     BATCH_CUDA(b, cudaMemsetAsync(b->ctr(), 0, sizeof(unsigned long long) * (2 + b->max_jobs),
                                   b->stream));
-    BATCH_CUDA(b, kLaunchers[occ](&q, b->grid[occ], b->stream));
+    const int grid = static_cast<int>((b->plan_warps + cell::kQueueWarps - 1) / cell::kQueueWarps);
+    BATCH_CUDA(b, kLaunchers[occ](&q, grid, b->stream));
   } else {
     for (uint32_t ph = 0; ph < 8 * sweeps; ++ph)
       BATCH_CUDA(b, kPhaseLaunchers[occ](&q, ph, b->stream));
@@ -430,6 +515,10 @@ smcx_status run_sweeps(smcx_batch* b, uint32_t sweeps, int tile, int sched, int 
   smcx_status s;
   if (b->dirty || b->queue_tile != tile) {
     s = build_queue(b, tile);
+    if (s != SMCX_OK) return s;
+  }
+  if (sched == 0 && (b->plan_tile != tile || b->plan_occ != occ)) {
+    s = build_plan(b, tile, occ);
     if (s != SMCX_OK) return s;
   }
   std::vector<uint8_t> table(sizeof(cell::JobDev) * b->max_jobs, 0);
@@ -605,7 +694,7 @@ smcx_status smcx_batch_create(uint32_t max_jobs, void* d_arena, size_t arena_byt
     e = cudaMemsetAsync(b->at(cl.stats), 0, sizeof(unsigned long long) * 8 * max_jobs, b->stream);
   if (e == cudaSuccess)
     e = cudaMemsetAsync(b->at(cl.qstats), 0, sizeof(unsigned long long) * 4, b->stream);
-  if (e == cudaSuccess)  // queue head, status word and per-job counters
+  if (e == cudaSuccess)  // status word and per-job counters (word 0 unused)
     e = cudaMemsetAsync(b->at(cl.ctr), 0, sizeof(unsigned long long) * (2 + max_jobs), b->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
   for (int o = 0; o < kOccCount && e == cudaSuccess; ++o) {

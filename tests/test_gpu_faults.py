@@ -1,5 +1,5 @@
 """Failure detection without a GPU fault: a device-side wait of the
-persistent batch queue is made to run out (the testing aid reports one more
+persistent batch schedule is made to run out (the testing aid reports one more
 work item for a job than it has, so the counter its next phase waits for is
 never reached); the wait gives up after its limit, the run returns
 SMCX_ETIMEOUT, the batch refuses further work, and the CUDA context stays
@@ -22,7 +22,7 @@ def test_device_wait_timeout_is_reported_and_context_survives(orc):
     b = Batch(4, 1 << 22, 1 << 14)
     for k in range(2):
         b.add(0, (8, 8, 8), 3, case["occ"], case["V"], 500.0 + 100 * k, 20, seed=k)
-    b.set_option(Batch.OPT_SCHEDULE, 0)  # the persistent queue (the one with device waits)
+    b.set_option(Batch.OPT_SCHEDULE, 0)  # the persistent schedule (the one with device waits)
     b.set_option(Batch.OPT_TEST_WAIT_TIMEOUT, 1)
     t0 = time.perf_counter()
     with pytest.raises(SmcxError) as err:
