@@ -152,6 +152,23 @@ smcx_status smcx_warren_cowley_sro(smcx_lattice* lat, uint32_t n_shells, uint64_
 /* Copies the occupancy to h_out (N bytes, canonical layout).  Synchronises. */
 smcx_status smcx_get_occupancy(smcx_lattice* lat, uint8_t* h_out);
 
+/* Starts copying the occupancy as it is now to h_out (N bytes, canonical
+   layout; the caller keeps it alive, pinned host memory makes the copy
+   asynchronous and fast) and returns without waiting.  The conversion to
+   the canonical layout is enqueued on the lattice's stream, so the copy
+   holds the occupancy of this point of the stream; the device-to-host copy
+   itself runs on a copy stream of the handle and overlaps the calls that
+   follow (a pair count, a sweep).  h_out is complete after
+   smcx_wait_occupancy.  Calls that use the handle's transfer buffer
+   (occupancy uploads and downloads, the composition profile) are ordered
+   after the copy on the device.  Starting another asynchronous copy before
+   waiting is allowed; smcx_wait_occupancy then waits for the last one. */
+smcx_status smcx_get_occupancy_async(smcx_lattice* lat, uint8_t* h_out);
+
+/* Waits until the copy started by the last smcx_get_occupancy_async has
+   reached the host (returns at once when there is none). */
+smcx_status smcx_wait_occupancy(smcx_lattice* lat);
+
 /* Replaces the occupancy by h_in (N bytes, canonical, ids < K, validated on
    the device; on EINVAL the occupancy is left as it was) and restarts the
    running energy (one pair count once a model is set).  The sweep counter

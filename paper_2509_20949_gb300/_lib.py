@@ -152,6 +152,8 @@ SIGNATURES = {
     "smcx_running_energy": (_st, [_vp, _P(ctypes.c_int64)]),
     "smcx_warren_cowley_sro": (_st, [_vp, ctypes.c_uint32, _vp, _vp]),
     "smcx_get_occupancy": (_st, [_vp, _vp]),
+    "smcx_get_occupancy_async": (_st, [_vp, _vp]),
+    "smcx_wait_occupancy": (_st, [_vp]),
     "smcx_set_occupancy": (_st, [_vp, _vp]),
     "smcx_get_sweep_counter": (_st, [_vp, _P(ctypes.c_uint32)]),
     "smcx_set_sweep_counter": (_st, [_vp, ctypes.c_uint32]),

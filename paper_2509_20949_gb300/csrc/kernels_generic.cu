@@ -265,6 +265,109 @@ __global__ void k_dev_to_canon(const Geom g, const uint8_t* __restrict__ occ,
   }
 }
 
+// Vector forms for rows of n_x % 4 == 0 (the canonical rows are then
+// 4 NB-byte aligned, the device rows are 16-byte aligned): a warp takes a
+// row (warps stride over rows), its lanes 4 cells at a time -- one 4 NB-byte
+// canonical access, one 4-byte access per device row group -- and the bytes
+// are (de)interleaved with byte permutes.  Chunks past n_x are the row
+// padding (zeros).
+
+// the 4 cells' byte of basis b from their canonical words (NB = 4: w0..w3;
+// NB = 2: lo = cells 0, 1 and hi = cells 2, 3)
+__device__ __forceinline__ void split4(const uint4 w, uint32_t (&o)[4]) {
+  const uint32_t t01 = __byte_perm(w.x, w.y, 0x5140), t23 = __byte_perm(w.z, w.w, 0x5140);
+  const uint32_t u01 = __byte_perm(w.x, w.y, 0x7362), u23 = __byte_perm(w.z, w.w, 0x7362);
+  o[0] = __byte_perm(t01, t23, 0x5410);
+  o[1] = __byte_perm(t01, t23, 0x7632);
+  o[2] = __byte_perm(u01, u23, 0x5410);
+  o[3] = __byte_perm(u01, u23, 0x7632);
+}
+
+template <int NB, bool PACK4>
+__global__ void k_canon_to_dev_v4(const Geom g, const uint8_t* __restrict__ canon,
+                                  uint8_t* __restrict__ occ, const unsigned int* __restrict__ skip) {
+  if (skip && *skip) return;
+  const uint32_t rows = static_cast<uint32_t>(g.n[1]) * g.n[2];
+  const uint32_t nxc = static_cast<uint32_t>(g.n[0]) / 4, pxc = static_cast<uint32_t>(g.px) / 4;
+  const uint32_t W = static_cast<uint32_t>(g.W);
+  const size_t grp_words = static_cast<size_t>(rows) * pxc;
+  const uint32_t lane = threadIdx.x & 31u;
+  const uint32_t warps = gridDim.x * (blockDim.x >> 5);
+  for (uint32_t r = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); r < rows; r += warps) {
+    const uint8_t* src_row = canon + static_cast<size_t>(r) * nxc * 4 * NB;
+    uint32_t* dst_row = reinterpret_cast<uint32_t*>(occ) + static_cast<size_t>(r) * pxc;
+    for (uint32_t c = lane; c < pxc; c += 32) {
+      uint32_t o[4] = {0u, 0u, 0u, 0u};  // per basis: the 4 cells' ids
+      if (c < nxc) {
+        if constexpr (NB == 4) {
+          split4(*reinterpret_cast<const uint4*>(src_row + 16 * c), o);
+        } else {
+          const uint2 v = *reinterpret_cast<const uint2*>(src_row + 8 * c);
+          o[0] = __byte_perm(v.x, v.y, 0x6420);
+          o[1] = __byte_perm(v.x, v.y, 0x7531);
+        }
+      }
+      if constexpr (!PACK4) {
+        // ids * W <= 255: the bytewise products do not carry
+#pragma unroll
+        for (int b = 0; b < NB; ++b) dst_row[b * grp_words + c] = o[b] * W;
+      } else {
+#pragma unroll
+        for (int b = 0; b < NB; b += 2) dst_row[(b >> 1) * grp_words + c] = o[b] | (o[b + 1] << 4);
+      }
+    }
+  }
+}
+
+template <int NB, bool PACK4>
+__global__ void k_dev_to_canon_v4(const Geom g, const uint8_t* __restrict__ occ,
+                                  uint8_t* __restrict__ canon) {
+  const uint32_t rows = static_cast<uint32_t>(g.n[1]) * g.n[2];
+  const uint32_t nxc = static_cast<uint32_t>(g.n[0]) / 4, pxc = static_cast<uint32_t>(g.px) / 4;
+  const uint32_t W = static_cast<uint32_t>(g.W);
+  const uint32_t inv = (65536u + W - 1u) / W;
+  const size_t grp_words = static_cast<size_t>(rows) * pxc;
+  const uint32_t lane = threadIdx.x & 31u;
+  const uint32_t warps = gridDim.x * (blockDim.x >> 5);
+  for (uint32_t r = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); r < rows; r += warps) {
+    const uint32_t* src_row = reinterpret_cast<const uint32_t*>(occ) + static_cast<size_t>(r) * pxc;
+    uint8_t* dst_row = canon + static_cast<size_t>(r) * nxc * 4 * NB;
+    for (uint32_t c = lane; c < nxc; c += 32) {
+      uint32_t o[4];  // per basis: the 4 cells' ids
+      if constexpr (!PACK4) {
+#pragma unroll
+        for (int b = 0; b < NB; ++b) {
+          const uint32_t v = src_row[b * grp_words + c];
+          if (W == 8u) {
+            o[b] = (v >> 3) & 0x1F1F1F1Fu;
+          } else {  // codes are sigma * W <= 255: sigma = (code * ceil(2^16 / W)) >> 16 exactly
+            uint32_t w = 0;
+#pragma unroll
+            for (int e = 0; e < 4; ++e) w |= ((((v >> (8 * e)) & 0xFFu) * inv) >> 16) << (8 * e);
+            o[b] = w;
+          }
+        }
+      } else {
+#pragma unroll
+        for (int b = 0; b < NB; b += 2) {
+          const uint32_t v = src_row[(b >> 1) * grp_words + c];
+          o[b] = v & 0x0F0F0F0Fu;
+          o[b + 1] = (v >> 4) & 0x0F0F0F0Fu;
+        }
+      }
+      if constexpr (NB == 4) {
+        // cell k = bytes k of o[0..3]: the transpose split4 is its own inverse
+        uint32_t w[4];
+        split4(make_uint4(o[0], o[1], o[2], o[3]), w);
+        *reinterpret_cast<uint4*>(dst_row + 16 * c) = make_uint4(w[0], w[1], w[2], w[3]);
+      } else {
+        *reinterpret_cast<uint2*>(dst_row + 8 * c) =
+            make_uint2(__byte_perm(o[0], o[1], 0x5140), __byte_perm(o[0], o[1], 0x7362));
+      }
+    }
+  }
+}
+
 // flag[0] |= 1 when a canonical byte is >= K: 16 bytes per thread, bytewise
 // compare of four bytes per word (__vcmpgeu4); the unaligned head and the
 // tail bytewise
@@ -330,6 +433,17 @@ cudaError_t launch_canon_to_dev(const Geom& g, const uint8_t* canon, uint8_t* oc
                                 const unsigned int* skip) {
   (void)n_cells;
   const uint32_t rows = static_cast<uint32_t>(g.n[1]) * g.n[2];
+  if (g.n[0] % 4 == 0) {
+    const uint32_t vb = grid_for(rows, 8, n_sm);  // a warp per row
+    if (g.nb == 2) {
+      if (g.pack4) k_canon_to_dev_v4<2, true><<<vb, 256, 0, st>>>(g, canon, occ, skip);
+      else k_canon_to_dev_v4<2, false><<<vb, 256, 0, st>>>(g, canon, occ, skip);
+    } else {
+      if (g.pack4) k_canon_to_dev_v4<4, true><<<vb, 256, 0, st>>>(g, canon, occ, skip);
+      else k_canon_to_dev_v4<4, false><<<vb, 256, 0, st>>>(g, canon, occ, skip);
+    }
+    return cudaGetLastError();
+  }
   const uint32_t blocks = grid_for(rows, 1, n_sm);
   if (g.nb == 2) {
     if (g.pack4) k_canon_to_dev<2, true><<<blocks, 256, 0, st>>>(g, canon, occ, skip);
@@ -345,6 +459,17 @@ cudaError_t launch_dev_to_canon(const Geom& g, const uint8_t* occ, uint8_t* cano
                                 uint32_t n_cells, int n_sm, cudaStream_t st) {
   (void)n_cells;
   const uint32_t rows = static_cast<uint32_t>(g.n[1]) * g.n[2];
+  if (g.n[0] % 4 == 0) {
+    const uint32_t vb = grid_for(rows, 8, n_sm);  // a warp per row
+    if (g.nb == 2) {
+      if (g.pack4) k_dev_to_canon_v4<2, true><<<vb, 256, 0, st>>>(g, occ, canon);
+      else k_dev_to_canon_v4<2, false><<<vb, 256, 0, st>>>(g, occ, canon);
+    } else {
+      if (g.pack4) k_dev_to_canon_v4<4, true><<<vb, 256, 0, st>>>(g, occ, canon);
+      else k_dev_to_canon_v4<4, false><<<vb, 256, 0, st>>>(g, occ, canon);
+    }
+    return cudaGetLastError();
+  }
   const uint32_t blocks = grid_for(rows, 1, n_sm);
   if (g.nb == 2) {
     if (g.pack4) k_dev_to_canon<2, true><<<blocks, 256, 0, st>>>(g, occ, canon);

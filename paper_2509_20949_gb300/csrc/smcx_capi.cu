@@ -231,8 +231,19 @@ struct smcx_lattice {
     std::vector<cudaEvent_t> ev;
   } tune;
 
+  // asynchronous read-back (smcx_get_occupancy_async): copy stream, the
+  // events after the conversion and after the copy, and whether a copy was
+  // started and not yet waited for
+  cudaStream_t copy = nullptr;
+  cudaEvent_t ev_conv = nullptr, ev_down = nullptr;
+  bool down_pending = false;
+
   ~smcx_lattice() {
     for (cudaEvent_t e : tune.ev) cudaEventDestroy(e);
+    if (copy) cudaStreamSynchronize(copy);
+    if (ev_conv) cudaEventDestroy(ev_conv);
+    if (ev_down) cudaEventDestroy(ev_down);
+    if (copy) cudaStreamDestroy(copy);
   }
 
   unsigned long long* stats() { return reinterpret_cast<unsigned long long*>(d_work + wl.stats); }
@@ -355,9 +366,17 @@ smcx_status validate_occupancy(const smcx_lattice_desc& d, const uint8_t* h) {
   return SMCX_OK;
 }
 
+// The transfer buffer (workspace scratch) is free on the lattice's stream
+// once an asynchronous read-back started earlier has copied it out.
+smcx_status scratch_guard(smcx_lattice* lat) {
+  if (lat->down_pending) SMCX_CUDA(lat, cudaStreamWaitEvent(lat->stream, lat->ev_down, 0));
+  return SMCX_OK;
+}
+
 // canonical host bytes -> workspace scratch -> (validated on the device) ->
 // device storage
 smcx_status upload_occupancy(smcx_lattice* lat, const uint8_t* h) {
+  if (scratch_guard(lat) != SMCX_OK) return SMCX_ECUDA;
   const Geom g = lat->geom();
   const uint32_t n_cells = static_cast<uint32_t>(lat->N / lat->nb);
   SMCX_CUDA(lat, cudaMemcpyAsync(lat->scratch(), h, lat->N, cudaMemcpyHostToDevice, lat->stream));
@@ -377,6 +396,7 @@ smcx_status upload_occupancy(smcx_lattice* lat, const uint8_t* h) {
 }
 
 smcx_status download_occupancy(smcx_lattice* lat, uint8_t* h) {
+  if (scratch_guard(lat) != SMCX_OK) return SMCX_ECUDA;
   const Geom g = lat->geom();
   const uint32_t n_cells = static_cast<uint32_t>(lat->N / lat->nb);
   SMCX_CUDA(lat, launch_dev_to_canon(g, lat->d_occ, lat->scratch(), n_cells, lat->n_sm,
@@ -1171,6 +1191,7 @@ smcx_status smcx_composition_profile(smcx_lattice* lat, uint32_t axis, const int
     return fail(SMCX_EINVAL, "need n_bins >= 1 and 1 <= length_h <= 2 n[axis]");
   if (n_bins * K > 8192 || 8 * n_bins * K > lat->N)
     return fail(SMCX_EINVAL, "too many bins (n_bins * K <= 8192 and 8 n_bins K <= sites)");
+  if (scratch_guard(lat) != SMCX_OK) return SMCX_ECUDA;
   const Geom g = lat->geom();
   auto* d_cnt = reinterpret_cast<unsigned long long*>(lat->scratch());
   const size_t bytes = sizeof(uint64_t) * n_bins * K;
@@ -1224,6 +1245,37 @@ smcx_status smcx_get_occupancy(smcx_lattice* lat, uint8_t* h_out) {
   if (s != SMCX_OK) return s;
   if (!h_out) return fail(SMCX_EINVAL, "null output");
   return download_occupancy(lat, h_out);
+}
+
+smcx_status smcx_get_occupancy_async(smcx_lattice* lat, uint8_t* h_out) {
+  smcx_status s = check_handle(lat);
+  if (s != SMCX_OK) return s;
+  if (!h_out) return fail(SMCX_EINVAL, "null output");
+  if (!lat->copy) {
+    SMCX_CUDA(lat, cudaStreamCreateWithFlags(&lat->copy, cudaStreamNonBlocking));
+    SMCX_CUDA(lat, cudaEventCreateWithFlags(&lat->ev_conv, cudaEventDisableTiming));
+    SMCX_CUDA(lat, cudaEventCreateWithFlags(&lat->ev_down, cudaEventDisableTiming));
+  }
+  if (scratch_guard(lat) != SMCX_OK) return SMCX_ECUDA;
+  const Geom g = lat->geom();
+  SMCX_CUDA(lat, launch_dev_to_canon(g, lat->d_occ, lat->scratch(),
+                                     static_cast<uint32_t>(lat->N / lat->nb), lat->n_sm,
+                                     lat->stream));
+  SMCX_CUDA(lat, cudaEventRecord(lat->ev_conv, lat->stream));
+  SMCX_CUDA(lat, cudaStreamWaitEvent(lat->copy, lat->ev_conv, 0));
+  SMCX_CUDA(lat, cudaMemcpyAsync(h_out, lat->scratch(), lat->N, cudaMemcpyDeviceToHost,
+                                 lat->copy));
+  SMCX_CUDA(lat, cudaEventRecord(lat->ev_down, lat->copy));
+  lat->down_pending = true;
+  return SMCX_OK;
+}
+
+smcx_status smcx_wait_occupancy(smcx_lattice* lat) {
+  if (!lat) return fail(SMCX_EINVAL, "null handle");
+  if (!lat->down_pending) return SMCX_OK;
+  SMCX_CUDA(lat, cudaEventSynchronize(lat->ev_down));
+  lat->down_pending = false;
+  return SMCX_OK;
 }
 
 smcx_status smcx_set_occupancy(smcx_lattice* lat, const uint8_t* h_in) {

@@ -178,6 +178,22 @@ class Lattice:
         check(self.L.smcx_get_occupancy(self.h, _host_ptr(out)))
         return out
 
+    def occupancy_async(self, out: np.ndarray) -> np.ndarray:
+        """Starts copying the occupancy as it is at this point of the stream
+        into `out` (a contiguous uint8 array of N bytes, best a view of
+        pinned host memory) and returns at once; the copy overlaps what is
+        enqueued next.  `out` is complete after wait_occupancy()."""
+        if out.dtype != np.uint8 or out.size != self.N or not out.flags["C_CONTIGUOUS"]:
+            raise ValueError("out must be a contiguous uint8 array of N bytes")
+        check(self.L.smcx_get_occupancy_async(self.h, _host_ptr(out)))
+        self._pending_out = out  # kept alive until the copy has landed
+        return out
+
+    def wait_occupancy(self):
+        """Waits for the copy started by the last occupancy_async()."""
+        check(self.L.smcx_wait_occupancy(self.h))
+        self._pending_out = None
+
     def set_occupancy(self, occ):
         occ = np.ascontiguousarray(occ, dtype=np.uint8)
         if occ.size != self.N:
