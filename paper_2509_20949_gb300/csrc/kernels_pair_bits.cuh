@@ -57,7 +57,7 @@ struct BCfg {
 struct BoxGeom {
   int BY, BZ, TY, TZ;  // box rows and rows with halo
   int NS, NSC;         // spans per staged row (ceil((nx + H) / 128)), centre spans
-  int nby, n_boxes;
+  int nby, nbz, n_boxes;  // boxes along y and z; box k = (y box k / nbz, z box k % nbz)
   int hstride;         // words between chunks h and h + 1 (NROWS * NS * 4)
   int pstride;         // words between planes (NQC * hstride)
   unsigned long long n_sites;
@@ -160,16 +160,44 @@ __global__ void __launch_bounds__(C::NT) k_pair_count_bits(const __grid_constant
 #pragma unroll
   for (int p = 0; p < C::NQ; ++p) scnt[p] = 0;
 
-  for (int box = blockIdx.x; box < bg.n_boxes; box += gridDim.x) {
-    const int y0 = (box % bg.nby) * bg.BY, z0 = (box / bg.nby) * bg.BZ;
+  // a block takes a contiguous run of boxes, z fastest within a column of
+  // boxes, so that consecutive boxes share 2H staged rows in z
+  const int k0 = static_cast<int>(static_cast<long long>(blockIdx.x) * bg.n_boxes / gridDim.x);
+  const int k1 = static_cast<int>(static_cast<long long>(blockIdx.x + 1) * bg.n_boxes / gridDim.x);
+  for (int box = k0; box < k1; ++box) {
+    const int y0 = (box / bg.nbz) * bg.BY, z0 = (box % bg.nbz) * bg.BZ;
+    // the previous box of this block is the one below in z: its staged rows
+    // tz in [BZ, BZ + 2H) are this box's rows [0, 2H)
+    const bool carry = box > k0 && box % bg.nbz != 0 && bg.BZ >= 2 * C::H;
     __syncthreads();  // the previous box's counting has finished reading the masks
-    // ---- masks of the box's rows plus halo: a warp per staged row, spans of
-    // 128 sites (4 per lane), up to 8 spans' loads in flight before their
-    // ballots
-    const int n_rows = C::NB * bg.TZ * bg.TY;
-    for (int r = warp; r < n_rows; r += NW) {
-      const int ty = r % bg.TY, t = r / bg.TY;
-      const int tz = t % bg.TZ, b = t / bg.TZ;
+    if (carry) {
+      const int n_cp = 4 * C::NQC * C::NB * 2 * C::H * bg.TY * bg.NS;
+      for (int i = tid; i < n_cp; i += C::NT) {
+        int u = i;
+        const int sp = u % bg.NS;
+        u /= bg.NS;
+        const int ty = u % bg.TY;
+        u /= bg.TY;
+        const int t = u % (2 * C::H);
+        u /= 2 * C::H;
+        const int b = u % C::NB;
+        const int plane = u / C::NB;  // j * NQC + h
+        const int src = ((b * bg.TZ + bg.BZ + t) * bg.TY + ty) * bg.NS + sp;
+        const int dst = ((b * bg.TZ + t) * bg.TY + ty) * bg.NS + sp;
+        uint4* base = reinterpret_cast<uint4*>(s_mask + plane * bg.hstride);
+        base[dst] = base[src];
+      }
+      __syncthreads();  // the carried rows are read before the new rows overwrite them
+    }
+    // ---- masks of the box's rows plus halo (only the rows not carried): a
+    // warp per staged row, spans of 128 sites (4 per lane), up to 8 spans'
+    // loads in flight before their ballots
+    const int tz0 = carry ? 2 * C::H : 0, nzs = bg.TZ - tz0;
+    const int n_rows = C::NB * nzs * bg.TY;
+    for (int rs = warp; rs < n_rows; rs += NW) {
+      const int ty = rs % bg.TY, t = rs / bg.TY;
+      const int tz = tz0 + t % nzs, b = t / nzs;
+      const int r = (b * bg.TZ + tz) * bg.TY + ty;  // staged row index
       const int gy = pmod(y0 - C::H + ty, ny), gz = pmod(z0 - C::H + tz, nz);
       // 8-bit storage: basis b's row holds codes sigma * W; 4-bit storage:
       // row group b / 2 holds sigma of bases b & ~1 (low nibble) and b | 1
@@ -334,10 +362,14 @@ bool box_for(const Geom& g, size_t budget, BoxGeom* bg, size_t* smem) {
   // a span past the last centre span only when the neighbours of the row's
   // last sites (x + H) do not fall into its wrapped tail; one padding chunk
   // after the masks keeps the next-span read of the last span in bounds
-  // (its bits only reach invalid centres)
+  // (its bits only reach invalid centres).  Box shapes, widest in y first
+  // (with the z rows carried from box to box, a box costs (BY + 2H) / BY
+  // staged rows per counted row).
   const int nsc = (g.n[0] + 127) / 128;
   const int ns = (g.n[0] + C::H + 127) / 128;
-  for (int by = 8, bz = 8; by >= 1;) {
+  constexpr int kShapes[][2] = {{16, 4}, {8, 8}, {8, 4}, {4, 4}, {4, 2}, {2, 2}, {2, 1}, {1, 1}};
+  for (const auto& sh : kShapes) {
+    const int by = sh[0], bz = sh[1];
     const int ty = by + 2 * C::H, tz = bz + 2 * C::H;
     const size_t bytes = (static_cast<size_t>(C::NB) * tz * ty * ns * C::SW + 4) * 4;
     const int hstride = C::NB * tz * ty * ns * 4;
@@ -349,16 +381,14 @@ bool box_for(const Geom& g, size_t budget, BoxGeom* bg, size_t* smem) {
       bg->NS = ns;
       bg->NSC = nsc;
       bg->nby = (g.n[1] + by - 1) / by;
-      bg->n_boxes = bg->nby * ((g.n[2] + bz - 1) / bz);
+      bg->nbz = (g.n[2] + bz - 1) / bz;
+      bg->n_boxes = bg->nby * bg->nbz;
       bg->n_sites = static_cast<unsigned long long>(C::NB) * g.n[0] * g.n[1] * g.n[2];
       bg->hstride = hstride;
       bg->pstride = C::NQC * hstride;
       *smem = bytes;
       return true;
     }
-    if (bz >= by) bz /= 2;
-    else by /= 2;
-    if (bz == 0) bz = 1;
   }
   return false;
 }
