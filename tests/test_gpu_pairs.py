@@ -2,8 +2,10 @@
 energy from them, through the C ABI, against the oracle's brute-force
 counts: row lengths that are and are not multiples of the 128-site spans of
 the bit-mask kernel, box rows that do not divide the lattice, 6 species,
-BCC shell 4 (two halo rows), FCC shells 1-4, thin lattices, and 4-bit
-storage (byte-tile kernel)."""
+BCC shell 4 (two halo rows), FCC shells 1-4, thin lattices, 4-bit storage,
+and lattices tall in z whose boxes outnumber the resident blocks, so that a
+block walks a run of boxes up a column and carries the halo rows of one
+box into the next (ragged last box of a column, runs across columns)."""
 import numpy as np
 import pytest
 
@@ -25,6 +27,9 @@ CASES = [
     (0, (129, 17, 10), 6, 4, 4),   # 4-bit, K = 6, ragged row length
     (1, (33, 5, 3), 6, 2, 4),
     (0, (31, 3, 2), 3, 3, 4),      # 4-bit, rows shorter than a span (wrap)
+    (0, (40, 20, 2602), 5, 3, 8),  # 2 x 651 boxes: carried rows, ragged y and z boxes
+    (0, (24, 16, 2800), 4, 4, 8),  # shell 4: two carried halo rows
+    (1, (20, 18, 1801), 5, 3, 4),  # FCC, 4-bit storage
 ]
 
 
