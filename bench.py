@@ -37,7 +37,7 @@ if ROOT not in sys.path:
 from paper_2509_20949_gb300 import inputs  # noqa: E402
 
 METRIC = ("attempted MC swaps/sec on 1 GB300 (plain single-lattice sweep; batched and served "
-          "forms in the line's batched/served objects)")
+          "forms in the line's batched/served/served_saturated objects)")
 UNIT = "swaps/s"
 
 
@@ -73,6 +73,9 @@ def parse():
                     help="plain mode: leave out the served (Poisson trace) measurement")
     ap.add_argument("--served-rate", type=float, default=1.0)
     ap.add_argument("--served-window", type=float, default=10.0)
+    ap.add_argument("--saturated-rate", type=float, default=5.0,
+                    help="plain mode: arrival rate of the second, saturating served trace (0 = none)")
+    ap.add_argument("--saturated-window", type=float, default=4.0)
     return ap.parse_args()
 
 
@@ -787,7 +790,7 @@ def main():
     trial_stats = {"unlike_frac": ts["unlike"] / ts["attempts"],
                    "accepted_frac": ts["accepted"] / ts["attempts"],
                    "accepted_per_unlike": ts["accepted"] / max(1, ts["unlike"])}
-    batched = served = None
+    batched = served = saturated = None
     if world == 1 and (not args.no_batched or not args.no_served):
         lat.close()
         del lat
@@ -795,8 +798,13 @@ def main():
         if not args.no_batched:
             batched = measure_batched(args.jobs, args.chunk)
         if not args.no_served:
+            # below saturation (latency), then a trace the device cannot keep up
+            # with alone (aggregate rate against FIFO one job at a time)
             served = measure_served(args.served_rate, args.served_window, args.budget_gb,
                                     args.chunk)
+            if args.saturated_rate > 0:
+                saturated = measure_served(args.saturated_rate, args.saturated_window,
+                                           args.budget_gb, args.chunk, seed=12)
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -822,6 +830,7 @@ def main():
             "trial_stats": trial_stats,
             "batched": batched,
             "served": served,
+            "served_saturated": saturated,
             "cpu_baseline": cpu,
             "clocks": clk,
             # per step: 8 colour phases + the pair count (K <= 6: bit-mask

@@ -92,3 +92,31 @@ def test_async_read_back_holds_its_point_of_the_stream():
     assert lat.running_energy() == lat.energy()
     lat.wait_occupancy()  # nothing pending: returns at once
     lat.close()
+
+
+def test_async_read_back_packed_and_invalid_upload_while_in_flight():
+    """4-bit FCC storage; an upload with an id >= K, issued while a read-back
+    is in flight, fails with EINVAL, leaves the lattice as it was and does
+    not disturb the copy."""
+    torch = require_cuda()
+    from paper_2509_20949_gb300 import SmcxError, _lib
+    from paper_2509_20949_gb300.lattice import Lattice
+    kind, n, K, M = 1, (40, 36, 30), 4, 3
+    occ = inputs.initial_occupancy(kind, n, K, 8)
+    V = inputs.epi_table(M, K, 0.03, 6)
+    lat = Lattice(kind, n, K, occ, seed=3, pack_bits=4)
+    lat.set_epi(V)
+    lat.sweep(2, 800.0)
+    now = lat.occupancy()
+    out = torch.empty(lat.N, dtype=torch.uint8, pin_memory=True).numpy()
+    lat.occupancy_async(out)
+    bad = now.copy()
+    bad[123] = K
+    with pytest.raises(SmcxError) as err:
+        lat.set_occupancy(bad)
+    assert err.value.status == _lib.SMCX_EINVAL
+    lat.wait_occupancy()
+    assert np.array_equal(out, now)
+    assert np.array_equal(lat.occupancy(), now)
+    assert lat.running_energy() == lat.energy()
+    lat.close()
