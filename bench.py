@@ -57,7 +57,7 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=6)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
-    ap.add_argument("--mode", default="plain", choices=["plain", "batch", "serve", "slab", "local"],
+    ap.add_argument("--mode", default="plain", choices=["plain", "batch", "serve", "slab", "local", "analysis", "exchange"],
                     help="plain: the single-lattice sweep (default); batch: 256 independent "
                          "lattices batched vs one at a time; serve: Poisson-arrival serving; "
                          "slab: one lattice decomposed along z over the ranks; local: the "
@@ -668,6 +668,138 @@ def run_serve(args):
     return 0
 
 
+def run_analysis(args):
+    """The analyses of Sec. 3.2 on the workload lattice after its warm-up
+    sweeps: the composition profile along a cylinder (one pass over the
+    lattice: 1 B/site of algorithmic traffic, against the HBM roofline) and
+    the first-shell clusters of the last species (union-find over all
+    sites).  Each timed `steps` times after `warmup` untimed calls; median."""
+    import torch
+
+    torch.cuda.set_device(0)
+    from paper_2509_20949_gb300.lattice import Lattice
+
+    w, N, desc = workload_config(args.workload)
+    V = inputs.epi_table(w["M"], w["K"], w["sigma"], w["epi_seed"])
+    occ = inputs.initial_occupancy(w["kind"], w["n"], w["K"], w["occ_seed"], w["fractions"])
+    lat = Lattice(w["kind"], w["n"], w["K"], occ, seed=w["seed"])
+    lat.set_epi(V)
+    lat.sweep(2, w["T_first"], stats=False)
+    n = w["n"]
+    origin = (n[0], n[1], 0)                      # the lattice's centre line (half units)
+    radius2 = (n[0] // 2) ** 2                    # a cylinder of radius n_x / 4 cells
+    length, n_bins = 2 * n[2], 64
+
+    def timed(f, k):
+        ts = []
+        for _ in range(k):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            r = f()
+            torch.cuda.synchronize()
+            ts.append(time.perf_counter() - t0)
+        return float(np.median(ts)), r
+
+    for _ in range(args.warmup):
+        lat.composition_profile(2, origin, radius2, length, n_bins)
+    clocks = ClockSampler(0)
+    clocks.start()
+    t_prof, prof = timed(lambda: lat.composition_profile(2, origin, radius2, length, n_bins),
+                         max(args.steps, 3))
+    species = [w["K"] - 1]
+    lat.clusters(species, cap=64)
+    t_cl, sizes = timed(lambda: lat.clusters(species, cap=64), 3)
+    clk = clocks.stop()
+    peak, peak_src = measured_peaks()
+    gbs = N / t_prof / 1e9
+    line = {"metric": "composition-profile pass over the lattice (Sec. 3.2), GB/s of site bytes read",
+            "value": gbs, "unit": "GB/s", "n_gpus": 1, "steps": max(args.steps, 3),
+            "warmup": args.warmup, "ms_per_step": 1e3 * t_prof, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
+            "mode": "analysis",
+            "config": {"workload": desc, "profile": f"axis z, radius^2 {radius2} half units^2, "
+                       f"length {length}, {n_bins} bins", "clusters": f"species {species}, first shell"},
+            "roofline": {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s",
+                         "frac": gbs / peak, "traffic": None, "kernel": "k_profile",
+                         "peak_source": peak_src},
+            "profile_sites_counted": int(prof.sum()),
+            "clusters": {"ms": 1e3 * t_cl, "sites_per_s": N / t_cl,
+                         "largest": [int(v) for v in sizes[:8]],
+                         "sites_of_species": int(np.count_nonzero(lat.occupancy() == species[0]))},
+            "clocks": clk, "gpu_launches": max(args.steps, 3)}
+    print(json.dumps(line), flush=True)
+    lat.close()
+    return 0
+
+
+def run_exchange(args):
+    """Replica exchange (parallel tempering, Sec. 2.2, Eqs. 6-7) through the
+    batch.  Throughput ladder: `--jobs` replicas (32 unless given) of one
+    system (BCC 128^3 x 2, K = 5, shells 1-3) on a geometric ladder of
+    600-1500 K; each round runs `--chunk` sweeps of every replica (one
+    graph-captured chunk), then one exchange round over the ladder (even and
+    odd neighbour pairs alternately).  value = attempted swaps / wall time of
+    `steps` rounds, exchanges included.  Mixing ladder: 64 replicas of BCC
+    16^3 x 2 on 800-1200 K, where neighbouring replicas' energies overlap,
+    for the acceptance of the exchanges."""
+    import torch
+
+    torch.cuda.set_device(0)
+    from paper_2509_20949_gb300.batch import Batch
+
+    def ladder_run(R, n, T0, T1):
+        kind, K, M = 0, 5, 3
+        V = inputs.epi_table(M, K, 0.02, 0)
+        occ = inputs.initial_occupancy(kind, n, K, 0)
+        sites = inputs.n_sites(kind, n)
+        temps = [T0 * (T1 / T0) ** (k / (R - 1)) for k in range(R)]
+        rounds = args.warmup + args.steps
+        b = Batch(R, Batch.control_bytes(R, sites) + R * Batch.job_bytes(kind, n, K) + (1 << 20),
+                  sites)
+        ladder = [b.add(kind, n, K, occ, V, T, rounds * args.chunk, seed=k)
+                  for k, T in enumerate(temps)]
+        acc_total, pairs_total, t_ex = 0, 0, []
+        torch.cuda.synchronize()
+        for r in range(args.warmup):
+            b.run(args.chunk)
+            ladder, _ = b.exchange(ladder, 7, r)
+        clocks = ClockSampler(0)
+        clocks.start()
+        t0 = time.perf_counter()
+        for r in range(args.warmup, rounds):
+            b.run(args.chunk)
+            te = time.perf_counter()
+            ladder, acc = b.exchange(ladder, 7, r)
+            t_ex.append(time.perf_counter() - te)
+            acc_total += acc
+            pairs_total += (R - (r & 1)) // 2
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        clk = clocks.stop()
+        b.close()
+        return {"replicas": R, "sites_each": sites, "T": [T0, T1],
+                "swaps_per_s": R * sites * args.chunk * args.steps / dt,
+                "ms_per_round": 1e3 * dt / args.steps,
+                "exchange_ms_per_round": 1e3 * float(np.median(t_ex)), "accepted": acc_total,
+                "attempted_pairs": pairs_total, "acceptance": acc_total / max(1, pairs_total),
+                "clocks": clk}
+
+    R = args.jobs if args.jobs != 256 else 32
+    big = ladder_run(R, (128, 128, 128), 600.0, 1500.0)
+    mix = ladder_run(64, (16, 16, 16), 800.0, 1200.0)
+    line = {"metric": "attempted MC swaps/sec of a replica-exchange ladder (batched, exchanges included)",
+            "value": big["swaps_per_s"], "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": big["ms_per_round"], "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+            "mode": "exchange",
+            "config": {"workload": f"{R} replicas of BCC 128^3 x 2 = {big['sites_each']} sites, K=5, "
+                       "shells 1-3, T geometric 600-1500 K",
+                       "step": f"{args.chunk} sweeps of every replica + one exchange round"},
+            "throughput_ladder": big, "mixing_ladder": mix, "clocks": big["clocks"]}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -680,6 +812,10 @@ def main():
         return run_slab(args)
     if args.mode == "local":
         return run_local(args)
+    if args.mode == "analysis":
+        return run_analysis(args)
+    if args.mode == "exchange":
+        return run_exchange(args)
     import torch
 
     world, rank, local = dist_setup()

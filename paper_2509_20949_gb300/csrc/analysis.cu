@@ -61,12 +61,128 @@ __global__ void k_profile(const Geom g, const uint8_t* __restrict__ occ, int axi
     if (s_h[i]) atomicAdd(&counts[i], static_cast<unsigned long long>(s_h[i]));
 }
 
+// The same counts, a warp per conventional row (z, y) and a lane per 4
+// cells of it (one 32-bit load per row group; bytes past n_x are the row
+// padding and masked).  The origin is brought into [0, 2n) once, so a
+// periodic difference takes one conditional add; bin_of[t] (shared, one
+// entry per half-unit position along the axis, 0xFFFF past `length`)
+// replaces the per-site division, and lanes of a warp that add to the same
+// (bin, species) counter combine first (__match_any_sync), so a row of one
+// bin costs one shared atomic per species present.  2 n_axis <= kBinTab.
+constexpr int kBinTab = 16384;
+
+__global__ void k_profile_rows(const Geom g, const uint8_t* __restrict__ occ, int axis, int o0,
+                               int o1, int o2, unsigned long long r2max, uint32_t length,
+                               uint32_t n_bins, unsigned long long* __restrict__ counts) {
+  extern __shared__ uint32_t s_h[];
+  const uint32_t K = static_cast<uint32_t>(g.K);
+  const uint32_t nh = n_bins * K;
+  uint16_t* const bin_of = reinterpret_cast<uint16_t*>(s_h + nh);
+  const int n2[3] = {2 * g.n[0], 2 * g.n[1], 2 * g.n[2]};
+  for (uint32_t i = threadIdx.x; i < nh; i += blockDim.x) s_h[i] = 0;
+  for (int t = threadIdx.x; t < n2[axis]; t += blockDim.x)
+    bin_of[t] = static_cast<uint32_t>(t) < length
+                    ? static_cast<uint16_t>(static_cast<unsigned long long>(t) * n_bins / length)
+                    : static_cast<uint16_t>(0xFFFF);
+  __syncthreads();
+  const int o[3] = {o0, o1, o2};  // in [0, 2n)
+  const int nx = g.n[0], ny = g.n[1], nz = g.n[2];
+  const uint32_t rows = static_cast<uint32_t>(ny) * nz;
+  const uint32_t lane = threadIdx.x & 31u;
+  const uint32_t warps = gridDim.x * (blockDim.x >> 5);
+  const uint32_t chunks = static_cast<uint32_t>(nx + 3) / 4;
+  const uint32_t inv = (65536u + static_cast<uint32_t>(g.W) - 1u) / static_cast<uint32_t>(g.W);
+  for (uint32_t r = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); r < rows; r += warps) {
+    const int y = static_cast<int>(r % ny), z = static_cast<int>(r / ny);
+    for (int b = 0; b < g.nb; ++b) {
+      // this row's y and z parts (h = 2c + basis; differences to o in [0, 2n))
+      int d[3];
+      d[1] = 2 * y + basis_comp(g.kind, b, 1) - o[1];
+      d[2] = 2 * z + basis_comp(g.kind, b, 2) - o[2];
+      d[1] += d[1] < 0 ? n2[1] : 0;
+      d[2] += d[2] < 0 ? n2[2] : 0;
+      unsigned long long r2row = 0;
+      uint32_t row_bin = 0xFFFFu;
+#pragma unroll
+      for (int e = 1; e < 3; ++e) {
+        if (e == axis) {
+          row_bin = bin_of[d[e]];
+        } else {
+          const long long dd = d[e] > g.n[e] ? d[e] - n2[e] : d[e];
+          r2row += static_cast<unsigned long long>(dd * dd);
+        }
+      }
+      if (axis != 0 && (row_bin == 0xFFFFu || r2row > r2max)) continue;  // warp-uniform
+      const int bx = basis_comp(g.kind, b, 0);
+      const uint8_t* row = occ + dev_row(g, g.pack4 ? b >> 1 : b, z, y);
+      const uint32_t shift = g.pack4 ? 4u * (b & 1) : 0u;
+      for (uint32_t c0 = 0; c0 < chunks; c0 += 32) {
+        const uint32_t c = c0 + lane;
+        uint32_t w = 0;
+        if (c < chunks) w = *reinterpret_cast<const uint32_t*>(row + 4 * c);  // rows pad to 16 B
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          const int x = static_cast<int>(4 * c) + e;
+          uint32_t key = 0xFFFFFFFFu;
+          if (c < chunks && x < nx) {
+            int dx = 2 * x + bx - o[0];
+            dx += dx < 0 ? n2[0] : 0;
+            uint32_t bin = row_bin;
+            unsigned long long r2 = r2row;
+            if (axis == 0) {
+              bin = bin_of[dx];
+            } else {
+              const long long dd = dx > nx ? dx - n2[0] : dx;
+              r2 += static_cast<unsigned long long>(dd * dd);
+            }
+            if (bin != 0xFFFFu && r2 <= r2max) {
+              const uint32_t code = (w >> (8 * e)) & 0xFFu;
+              const uint32_t sp = g.pack4 ? (code >> shift) & 15u : (code * inv) >> 16;
+              key = bin * K + sp;
+            }
+          }
+          const unsigned act = __ballot_sync(0xffffffffu, key != 0xFFFFFFFFu);
+          if (key != 0xFFFFFFFFu) {
+            const unsigned same = __match_any_sync(act, key);
+            if (lane == static_cast<uint32_t>(__ffs(same) - 1)) atomicAdd(&s_h[key], __popc(same));
+          }
+        }
+      }
+    }
+  }
+  __syncthreads();
+  for (uint32_t i = threadIdx.x; i < nh; i += blockDim.x)
+    if (s_h[i]) atomicAdd(&counts[i], static_cast<unsigned long long>(s_h[i]));
+}
+
 }  // namespace
 
 cudaError_t launch_profile(const Geom& g, const uint8_t* occ, int axis, const int* origin_h,
                            unsigned long long r2max, uint32_t length, uint32_t n_bins,
                            unsigned long long* counts, int n_sm, cudaStream_t st) {
   const uint32_t n_cells = static_cast<uint32_t>(g.n[0]) * g.n[1] * g.n[2];
+  if (2 * g.n[axis] <= kBinTab) {
+    const uint32_t rows = static_cast<uint32_t>(g.n[1]) * g.n[2];
+    uint32_t grid = (rows + 7) / 8;  // a warp per row
+    if (grid > static_cast<uint32_t>(n_sm) * 8) grid = static_cast<uint32_t>(n_sm) * 8;
+    if (grid == 0) grid = 1;
+    const size_t smem = sizeof(uint32_t) * n_bins * static_cast<uint32_t>(g.K) +
+                        sizeof(uint16_t) * 2 * g.n[axis];
+    int o[3];
+    for (int d = 0; d < 3; ++d) {
+      const int m = 2 * g.n[d];
+      o[d] = ((origin_h[d] % m) + m) % m;
+    }
+    if (smem > 48 * 1024) {
+      const cudaError_t e = cudaFuncSetAttribute(k_profile_rows,
+                                                 cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 static_cast<int>(smem));
+      if (e != cudaSuccess) return e;
+    }
+    k_profile_rows<<<grid, 256, smem, st>>>(g, occ, axis, o[0], o[1], o[2], r2max, length, n_bins,
+                                            counts);
+    return cudaGetLastError();
+  }
   uint32_t grid = (n_cells + 255) / 256;
   if (grid > static_cast<uint32_t>(n_sm) * 8) grid = static_cast<uint32_t>(n_sm) * 8;
   if (grid == 0) grid = 1;

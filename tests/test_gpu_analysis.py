@@ -14,6 +14,9 @@ pytestmark = pytest.mark.gpu
     (0, (20, 18, 22), 5, 8, 2, (7, -3, 40), 50, 30, 6),
     (1, (16, 14, 12), 4, 8, 0, (3, 3, 3), 20, 32, 8),
     (0, (12, 12, 12), 6, 4, 1, (0, 0, 0), 10 ** 6, 24, 12),
+    (0, (13, 10, 9), 9, 8, 0, (30, 5, -7), 40, 20, 5),   # n_x % 4 != 0, K > 6 (codes = ids)
+    (1, (7, 9, 11), 6, 8, 2, (1, 2, 3), 12, 22, 11),     # K = 6 (codes 5 sigma), short rows
+    (1, (9, 8, 10), 5, 4, 1, (4, 40, 2), 30, 16, 4),     # FCC, 4-bit storage, axis y
 ])
 def test_profile_matches_oracle(orc, kind, n, K, pack, axis, o, r2, length, bins):
     require_cuda()
