@@ -62,8 +62,8 @@ __global__ void k_profile(const Geom g, const uint8_t* __restrict__ occ, int axi
 }
 
 // The same counts, a warp per conventional row (z, y) and a lane per 4
-// cells of it (one 32-bit load per row group; bytes past n_x are the row
-// padding and masked).  The origin is brought into [0, 2n) once, so a
+// cells of it (32-bit loads per row group, up to 8 in flight; bytes past
+// n_x are the row padding and masked).  The origin is brought into [0, 2n) once, so a
 // periodic difference takes one conditional add; bin_of[t] (shared, one
 // entry per half-unit position along the axis, 0xFFFF past `length`)
 // replaces the per-site division, and lanes of a warp that add to the same
@@ -116,35 +116,44 @@ __global__ void k_profile_rows(const Geom g, const uint8_t* __restrict__ occ, in
       const int bx = basis_comp(g.kind, b, 0);
       const uint8_t* row = occ + dev_row(g, g.pack4 ? b >> 1 : b, z, y);
       const uint32_t shift = g.pack4 ? 4u * (b & 1) : 0u;
-      for (uint32_t c0 = 0; c0 < chunks; c0 += 32) {
-        const uint32_t c = c0 + lane;
-        uint32_t w = 0;
-        if (c < chunks) w = *reinterpret_cast<const uint32_t*>(row + 4 * c);  // rows pad to 16 B
+      // up to 8 loads of the row in flight before their sites are counted
+      for (uint32_t c8 = 0; c8 < chunks; c8 += 256) {
+        uint32_t wv[8];
 #pragma unroll
-        for (int e = 0; e < 4; ++e) {
-          const int x = static_cast<int>(4 * c) + e;
-          uint32_t key = 0xFFFFFFFFu;
-          if (c < chunks && x < nx) {
-            int dx = 2 * x + bx - o[0];
-            dx += dx < 0 ? n2[0] : 0;
-            uint32_t bin = row_bin;
-            unsigned long long r2 = r2row;
-            if (axis == 0) {
-              bin = bin_of[dx];
-            } else {
-              const long long dd = dx > nx ? dx - n2[0] : dx;
-              r2 += static_cast<unsigned long long>(dd * dd);
+        for (int k = 0; k < 8; ++k) {
+          const uint32_t c = c8 + 32u * k + lane;
+          wv[k] = c < chunks ? *reinterpret_cast<const uint32_t*>(row + 4 * c) : 0u;  // rows pad to 16 B
+        }
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+          if (c8 + 32u * k >= chunks) break;  // warp-uniform
+          const uint32_t c = c8 + 32u * k + lane;
+#pragma unroll
+          for (int e = 0; e < 4; ++e) {
+            const int x = static_cast<int>(4 * c) + e;
+            uint32_t key = 0xFFFFFFFFu;
+            if (c < chunks && x < nx) {
+              int dx = 2 * x + bx - o[0];
+              dx += dx < 0 ? n2[0] : 0;
+              uint32_t bin = row_bin;
+              unsigned long long r2 = r2row;
+              if (axis == 0) {
+                bin = bin_of[dx];
+              } else {
+                const long long dd = dx > nx ? dx - n2[0] : dx;
+                r2 += static_cast<unsigned long long>(dd * dd);
+              }
+              if (bin != 0xFFFFu && r2 <= r2max) {
+                const uint32_t code = (wv[k] >> (8 * e)) & 0xFFu;
+                const uint32_t sp = g.pack4 ? (code >> shift) & 15u : (code * inv) >> 16;
+                key = bin * K + sp;
+              }
             }
-            if (bin != 0xFFFFu && r2 <= r2max) {
-              const uint32_t code = (w >> (8 * e)) & 0xFFu;
-              const uint32_t sp = g.pack4 ? (code >> shift) & 15u : (code * inv) >> 16;
-              key = bin * K + sp;
+            const unsigned act = __ballot_sync(0xffffffffu, key != 0xFFFFFFFFu);
+            if (key != 0xFFFFFFFFu) {
+              const unsigned same = __match_any_sync(act, key);
+              if (lane == static_cast<uint32_t>(__ffs(same) - 1)) atomicAdd(&s_h[key], __popc(same));
             }
-          }
-          const unsigned act = __ballot_sync(0xffffffffu, key != 0xFFFFFFFFu);
-          if (key != 0xFFFFFFFFu) {
-            const unsigned same = __match_any_sync(act, key);
-            if (lane == static_cast<uint32_t>(__ffs(same) - 1)) atomicAdd(&s_h[key], __popc(same));
           }
         }
       }
