@@ -1235,8 +1235,11 @@ smcx_status smcx_clusters(smcx_lattice* lat, uint32_t species_mask, void* d_scra
   SMCX_CUDA(lat, cudaMemcpyAsync(all.data(), lab, sizeof(uint32_t) * all.size(),
                                  cudaMemcpyDeviceToHost, lat->stream));
   SMCX_CUDA(lat, cudaStreamSynchronize(lat->stream));
-  std::sort(all.begin(), all.end(), [](uint32_t a, uint32_t b) { return a > b; });
-  for (uint64_t k = 0; k < cap && k < all.size(); ++k) sizes[k] = all[k];
+  // only the largest `cap` sizes are returned, in descending order
+  const size_t top = static_cast<size_t>(std::min<uint64_t>(cap, all.size()));
+  std::partial_sort(all.begin(), all.begin() + top, all.end(),
+                    [](uint32_t a, uint32_t b) { return a > b; });
+  for (size_t k = 0; k < top; ++k) sizes[k] = all[k];
   return SMCX_OK;
 }
 
