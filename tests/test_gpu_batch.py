@@ -173,3 +173,34 @@ def test_online_tuning_converges_without_changing_results():
         occ_a, st, E = _alone(c)
         assert np.array_equal(r["occ"], occ_a), k
         assert r["stats"] == st and r["energy"] == E and r["sweeps"] == 30
+
+
+def test_persistent_plan_with_many_jobs_and_segments():
+    """The persistent schedule's plan over 400 jobs of uneven size (many
+    segments per warp for the small ones, one job spread over many warps):
+    the jobs end as they do alone, including jobs that stop in the middle of
+    a chunk."""
+    require_cuda()
+    from paper_2509_20949_gb300.batch import Batch
+    jobs = _jobs(9, 399, nmin=4, nmax=9)
+    big = make_case(1, (44, 40, 36), 5, 3, seed=900, sigma=0.03, epi_seed=901, occ_seed=902)
+    big.update(T=900.0, sweeps=7)
+    jobs.append(big)
+    b = _batch(max_jobs=400, arena=1 << 28, transfer=1 << 21)
+    b.set_option(Batch.OPT_SCHEDULE, 0)
+    b.set_option(Batch.OPT_TILE, 0)
+    ids = [_add(b, c) for c in jobs]
+    done = set()
+    for _ in range(20):
+        b.run(5)
+        done |= set(b.poll())
+        if len(done) == len(jobs):
+            break
+    assert done == set(ids)
+    assert b.tuning()["schedule"] == 0
+    for k in list(range(0, len(jobs), 37)) + [len(jobs) - 1]:
+        r = b.result(ids[k])
+        occ, st, E = _alone(jobs[k])
+        assert np.array_equal(r["occ"], occ), k
+        assert r["stats"] == st and r["energy"] == E, k
+    b.close()
