@@ -6,10 +6,11 @@
 // shared-memory tiles: they stay in L2) and for batches of many jobs, whose
 // work items (32 cells of one job and colour phase, one per lane) are run
 // either by one launch per colour phase or by one persistent launch per
-// chunk of sweeps following a plan (k_sweep_cells_phase / k_sweep_cells_queue).  Works on any
-// lattice with at least 4 conventional cells per dimension (then no two
-// shell vectors reach the same site, so the swapped pair's mutual bond is
-// the only term to remove from the raw neighbour counts).
+// chunk of sweeps following a plan (k_sweep_cells_phase /
+// k_sweep_cells_queue).  Works on any lattice with at least 4 conventional
+// cells per dimension (then no two shell vectors reach the same site, so
+// the swapped pair's mutual bond is the only term to remove from the raw
+// neighbour counts).
 //
 // Neighbour addressing: for the anchor's conventional cell the wrapped
 // coordinates of offsets -3..3 along each axis are tabulated once (as byte

@@ -4,9 +4,9 @@
 //
 // The caller hands over one device arena.  Its head holds the control area
 // (device job table, threshold and difference tables per job slot, per-job
-// statistics, the work-item order and queue counters, a transfer buffer);
-// the rest is a job heap from which every admitted lattice gets its
-// occupancy (first-fit, coalescing free list).  Work items are 32 active
+// statistics, the work-item order, the persistent plan and per-job phase
+// counters, two transfer buffers); the rest is a job heap from which every
+// admitted lattice gets its occupancy (first-fit, coalescing free list).  Work items are 32 active
 // link cells of one job and colour phase (kernels_cell.cuh), ordered within
 // a phase with the jobs whose largest cells have the most trials first.  Two
 // schedules run a chunk of S sweeps of every active job: the persistent
@@ -511,7 +511,7 @@ uint32_t advance_jobs(smcx_batch* b, const std::vector<uint32_t>& slots, uint32_
 smcx_status run_sweeps(smcx_batch* b, uint32_t sweeps, int tile, int sched, int occ,
                        bool use_graph, uint32_t* n_finished, uint64_t* trials, float* ms,
                        bool async = false) {
-  TraceRange trace(sched == 0 ? "smcx_batch_chunk_queue" : "smcx_batch_chunk_phases");
+  TraceRange trace(sched == 0 ? "smcx_batch_chunk_persistent" : "smcx_batch_chunk_phases");
   smcx_status s;
   if (b->dirty || b->queue_tile != tile) {
     s = build_queue(b, tile);
