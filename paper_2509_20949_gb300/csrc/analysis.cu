@@ -92,6 +92,7 @@ __global__ void k_profile_rows(const Geom g, const uint8_t* __restrict__ occ, in
   const uint32_t warps = gridDim.x * (blockDim.x >> 5);
   const uint32_t chunks = static_cast<uint32_t>(nx + 3) / 4;
   const uint32_t inv = (65536u + static_cast<uint32_t>(g.W) - 1u) / static_cast<uint32_t>(g.W);
+  const bool reg_count = axis != 0 && K <= 8u && nx < 65536;
   for (uint32_t r = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); r < rows; r += warps) {
     const int y = static_cast<int>(r % ny), z = static_cast<int>(r / ny);
     for (int b = 0; b < g.nb; ++b) {
@@ -116,6 +117,51 @@ __global__ void k_profile_rows(const Geom g, const uint8_t* __restrict__ occ, in
       const int bx = basis_comp(g.kind, b, 0);
       const uint8_t* row = occ + dev_row(g, g.pack4 ? b >> 1 : b, z, y);
       const uint32_t shift = g.pack4 ? 4u * (b & 1) : 0u;
+      // along y or z the row has one bin: with K <= 8 and rows shorter than
+      // 2^16 cells each lane counts species in 16-bit fields (species s in
+      // field s & 3 of reg[s >> 2]; a field's sum over the warp is at most
+      // n_x), and the warp adds the row's counts once
+      if (reg_count) {
+        unsigned long long reg[2] = {0ull, 0ull};
+        for (uint32_t c8 = 0; c8 < chunks; c8 += 256) {
+          uint32_t wv[8];
+#pragma unroll
+          for (int k = 0; k < 8; ++k) {
+            const uint32_t c = c8 + 32u * k + lane;
+            wv[k] = c < chunks ? *reinterpret_cast<const uint32_t*>(row + 4 * c) : 0u;
+          }
+#pragma unroll
+          for (int k = 0; k < 8; ++k) {
+            const uint32_t c = c8 + 32u * k + lane;
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+              const int x = static_cast<int>(4 * c) + e;
+              if (c >= chunks || x >= nx) continue;
+              int dx = 2 * x + bx - o[0];
+              dx += dx < 0 ? n2[0] : 0;
+              const long long dd = dx > nx ? dx - n2[0] : dx;
+              if (r2row + static_cast<unsigned long long>(dd * dd) > r2max) continue;
+              const uint32_t code = (wv[k] >> (8 * e)) & 0xFFu;
+              const uint32_t sp = g.pack4 ? (code >> shift) & 15u : (code * inv) >> 16;
+              const unsigned long long one = 1ull << (16 * (sp & 3u));
+              if (sp < 4u) reg[0] += one;
+              else reg[1] += one;
+            }
+          }
+        }
+        uint32_t f[4];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          f[2 * h] = __reduce_add_sync(0xffffffffu, static_cast<uint32_t>(reg[h]));
+          f[2 * h + 1] = __reduce_add_sync(0xffffffffu, static_cast<uint32_t>(reg[h] >> 32));
+        }
+        if (lane == 0)
+          for (uint32_t sp = 0; sp < K; ++sp) {
+            const uint32_t v = (f[sp >> 1] >> (16 * (sp & 1u))) & 0xFFFFu;
+            if (v) atomicAdd(&s_h[row_bin * K + sp], v);
+          }
+        continue;
+      }
       // up to 8 loads of the row in flight before their sites are counted
       for (uint32_t c8 = 0; c8 < chunks; c8 += 256) {
         uint32_t wv[8];

@@ -17,6 +17,7 @@ pytestmark = pytest.mark.gpu
     (0, (13, 10, 9), 9, 8, 0, (30, 5, -7), 40, 20, 5),   # n_x % 4 != 0, K > 6 (codes = ids)
     (1, (7, 9, 11), 6, 8, 2, (1, 2, 3), 12, 22, 11),     # K = 6 (codes 5 sigma), short rows
     (1, (9, 8, 10), 5, 4, 1, (4, 40, 2), 30, 16, 4),     # FCC, 4-bit storage, axis y
+    (0, (12, 10, 9), 12, 8, 2, (3, 4, 5), 60, 18, 6),    # K > 8 along z: warp-combined atomics
 ])
 def test_profile_matches_oracle(orc, kind, n, K, pack, axis, o, r2, length, bins):
     require_cuda()
