@@ -71,8 +71,10 @@ class Server:
                 continue
             self.running[jid] = (ticket, job, arr)
             self.progress[jid] = 0
-            # every job still waiting ahead of this one has been overtaken once more
+            # every job still waiting ahead of this one has been overtaken once
+            # more; one that has reached the limit stops the later ones
             remaining = collections.deque((t, j, a, b + 1) for (t, j, a, b) in remaining)
+            starving = any(b >= self.max_bypass for (_, _, _, b) in remaining)
         self.queue = remaining
 
     def _account(self, jids):
